@@ -1,0 +1,200 @@
+/*
+ * gs.h — C ABI of the GB300 (sm_103a) 3D Gaussian Splatting tile rasterizer
+ * with Speedy-Splat Gaussian-to-tile localization.
+ *
+ * The pipeline follows the six functions of the 3D-GS forward renderer
+ * (Sec. 3.2 and Table 1 of Speedy-Splat, arXiv 2412.00578):
+ *   gs_preprocess   per-Gaussian projection, colour and tile count  (Sec. 3.2.1)
+ *   gs_intersect    InclusiveSum + duplicateWithKeys                 (Sec. 3.2.2)
+ *   gs_sort         RadixSort of the (tile | depth) keys             (Sec. 3.2.2)
+ *   gs_tile_ranges  identifyTileRanges                               (Sec. 3.2.2)
+ *   gs_render       front-to-back alpha blending per pixel           (Sec. 3.2.3)
+ * with the tile-localization mode chosen per call: the 3D-GS 3-sigma square
+ * (Eq. radius), SnugBox (Sec. 4.1.1) or AccuTile (Sec. 4.1.2, Algorithm 1).
+ *
+ * Conventions for every entry point:
+ *   - All array arguments are DEVICE pointers owned by the caller, except
+ *     where a comment says "host".  The library never allocates device memory;
+ *     gs_frame_sizes() tells the caller what to allocate.
+ *   - Every call is asynchronous on the context's CUDA stream, except the ones
+ *     documented as synchronising (gs_intersect with a non-NULL num_keys,
+ *     gs_read_status).
+ *   - Errors are returned as gs_status; gs_last_error() gives a message.  No
+ *     call aborts, throws or traps.  Errors detected on the device (key
+ *     capacity exceeded, a bounded wait that ran out) are recorded in the
+ *     frame's status words and reported by gs_read_status().
+ *   - One context per host thread.
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gs_status {
+    GS_OK = 0,
+    GS_ERR_INVALID = 1,   /* bad argument (null pointer, size, mode, tile)        */
+    GS_ERR_OOM = 2,       /* reserved: the library does not allocate device memory */
+    GS_ERR_CAPACITY = 3,  /* more keys than gs_frame.key_capacity                 */
+    GS_ERR_CUDA = 4,      /* a CUDA runtime call failed                            */
+    GS_ERR_TIMEOUT = 5    /* a bounded device-side wait gave up                    */
+} gs_status;
+
+typedef enum gs_mode {
+    GS_MODE_3SIGMA = 0,   /* 3D-GS square of radius ceil(3 sqrt(lambda_max)), Eq. radius */
+    GS_MODE_SNUGBOX = 1,  /* tight box of the opacity-aware ellipse, Sec. 4.1.1       */
+    GS_MODE_ACCUTILE = 2  /* exact tiles of that ellipse, Sec. 4.1.2, Algorithm 1     */
+} gs_mode;
+
+/* Device status word flags (gs_read_status). */
+#define GS_FLAG_CAPACITY 1u   /* keys did not fit: nothing was emitted            */
+#define GS_FLAG_TIMEOUT  2u   /* a sort look-back wait exceeded its bound         */
+
+/* Gaussian parameter set G_i = {mu, s, r, h, sigma} (Sec. 3.1), planar
+ * structure of arrays, float32, device memory, read only.
+ *   means     [3][n]       x plane, y plane, z plane
+ *   scales    [3][n]       activated (exp applied)
+ *   rotations [4][n]       quaternion w, x, y, z (normalised by the kernel)
+ *   opacities [n]          activated (sigmoid applied)
+ *   sh        [16][3][n]   coefficient k, channel c at sh[(k*3 + c)*n + i];
+ *                          only the first (sh_degree+1)^2 coefficients are read */
+typedef struct gs_scene {
+    int64_t n;
+    int32_t sh_degree;  /* 0..3 */
+    const float* means;
+    const float* scales;
+    const float* rotations;
+    const float* opacities;
+    const float* sh;
+} gs_scene;
+
+/* Pinhole camera (host struct, passed by pointer, copied by value).  OpenCV
+ * axes: x right, y down, z forward.  Pixel (i, j) sits at the point (i, j).
+ * viewmat is the row-major 3x4 world-to-camera transform [R | t]; campos
+ * the camera centre in world coordinates (for the SH view direction).
+ * Gaussians with view depth <= near_z are culled. */
+typedef struct gs_camera {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float tan_fovx, tan_fovy;
+    float near_z;
+    float viewmat[12];
+    float campos[3];
+} gs_camera;
+
+/* Raster configuration: tile edge (8, 16 or 32 pixels), gs_mode, background. */
+typedef struct gs_raster_cfg {
+    int32_t tile;
+    int32_t mode;
+    float bg[3];
+} gs_raster_cfg;
+
+/* Per-frame buffers, all device memory owned by the caller, sized by
+ * gs_frame_sizes() for (n_capacity, width, height, tile, key_capacity).
+ * Layouts:
+ *   proj     [3][n_capacity][4] float: plane 0 = (u, v, opacity, depth),
+ *            plane 1 = conic (a, b, c) and t = 2 log(255 sigma),
+ *            plane 2 = (r, g, b, radius as int32 bits).  Written only for
+ *            Gaussians with a non-zero tile count.
+ *   counts   [n_capacity] int32: tiles touched in the preprocessed mode.
+ *   keys     [2][key_capacity] uint64: (tile id << 32) | float bits of depth.
+ *   vals     [2][key_capacity] uint32: Gaussian index.
+ *            After gs_sort the sorted pairs are in keys[0..K), vals[0..K).
+ *   ranges   [tiles][2] uint32: [start, end) of each tile in the sorted list.
+ *   image    [3][height][width] float, final_T [height][width] float,
+ *   last     [height][width] uint32: 1-based position, in its tile's list, of
+ *            the last Gaussian that contributed to the pixel (0: none).
+ *   scratch  library working memory (status words, scan partials, sort
+ *            histograms and look-back tables); contents are private. */
+typedef struct gs_frame {
+    int64_t n_capacity;
+    int64_t key_capacity;   /* <= GS_MAX_KEYS */
+    int32_t width, height, tile;
+    float* proj;
+    int32_t* counts;
+    uint64_t* keys;
+    uint32_t* vals;
+    uint32_t* ranges;
+    float* image;
+    float* final_T;
+    uint32_t* last;
+    void* scratch;
+} gs_frame;
+
+#define GS_MAX_KEYS ((int64_t)((1u << 30) - 1))
+
+/* Byte sizes of the gs_frame buffers (host output). */
+typedef struct gs_frame_bytes {
+    int64_t proj, counts, keys, vals, ranges, image, final_T, last, scratch;
+} gs_frame_bytes;
+
+typedef struct gs_context gs_context;
+
+/* Create a context bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t; NULL = legacy default stream).  *out receives the
+ * context; free it with gs_destroy.  Allocates host memory only. */
+gs_status gs_create(int device, void* cuda_stream, gs_context** out);
+void gs_destroy(gs_context* ctx);
+gs_status gs_set_stream(gs_context* ctx, void* cuda_stream);
+/* Message of the last error on this context (never NULL). */
+const char* gs_last_error(const gs_context* ctx);
+/* Number of kernels this context has launched so far. */
+int64_t gs_launch_count(const gs_context* ctx);
+
+/* Sizes of the per-frame buffers.  Returns GS_ERR_INVALID for tile not in
+ * {8,16,32}, non-positive sizes, or key_capacity > GS_MAX_KEYS. */
+gs_status gs_frame_sizes(int64_t n_capacity, int32_t width, int32_t height, int32_t tile, int64_t key_capacity,
+                         gs_frame_bytes* out);
+
+/* Preprocess (Sec. 3.2.1): for each Gaussian, view transform and near cull,
+ * projected mean and depth, Sigma3D = R S S^T R^T, Sigma2D = J W Sigma3D W^T J^T
+ * (+0.3 I), its inverse (the conic), t = 2 log(255 sigma) (Sec. 4.1), the 3D-GS
+ * radius, the SH colour, and the number of tiles touched in cfg->mode.
+ * Writes frame->proj (for counted Gaussians) and frame->counts[0..n). */
+gs_status gs_preprocess(gs_context* ctx, const gs_scene* scene, const gs_camera* cam, const gs_raster_cfg* cfg,
+                        const gs_frame* frame);
+
+/* InclusiveSum of the counts and duplicateWithKeys (Sec. 3.2.2): recomputes
+ * each Gaussian's tiles in cfg->mode (which must be the mode the counts were
+ * made with) and writes one (key, value) pair per (Gaussian, tile) into
+ * keys[0]/vals[0], Gaussians in index order.  The key total K is kept on the
+ * device.  If K > key_capacity nothing is emitted and GS_FLAG_CAPACITY is set.
+ * num_keys: NULL for a fully asynchronous call; otherwise the call
+ * synchronises the stream, stores K (host) and returns GS_ERR_CAPACITY if
+ * K exceeds the capacity. */
+gs_status gs_intersect(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame,
+                       int64_t* num_keys);
+
+/* RadixSort (Sec. 3.2.2): stable LSD radix sort of the K pairs by key, over
+ * the 32 depth bits plus ceil(log2(tiles)) tile bits, in an even number of
+ * onesweep passes, result in keys[0]/vals[0].  Uses frame->scratch. */
+gs_status gs_sort(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame);
+
+/* identifyTileRanges (Sec. 3.2.2): ranges[tile] = [start, end) of the tile's
+ * entries in the sorted keys; [0, 0) for empty tiles. */
+gs_status gs_tile_ranges(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame);
+
+/* render (Sec. 3.2.3, Eqs. render_alpha, 2d_gaussian_scalar, contribution):
+ * for each pixel, walk its tile's Gaussians front to back; a Gaussian counts
+ * where q <= t (alpha >= 1/255), alpha = min(0.99, sigma exp(-q/2)); stop
+ * before a Gaussian that would bring the transmittance below 1e-4; finally
+ * add T * bg.  Writes image, final_T and last. */
+gs_status gs_render(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame);
+
+/* The five stages above in one call, with no host synchronisation. */
+gs_status gs_forward(gs_context* ctx, const gs_scene* scene, const gs_camera* cam, const gs_raster_cfg* cfg,
+                     const gs_frame* frame);
+
+/* Synchronise the stream and read the frame's device status: the key total
+ * K and the GS_FLAG_* bits (both host outputs, nullable).  Returns
+ * GS_ERR_CAPACITY or GS_ERR_TIMEOUT if the corresponding flag is set. */
+gs_status gs_read_status(gs_context* ctx, const gs_frame* frame, int64_t* num_keys, uint32_t* flags);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H_ */

@@ -319,7 +319,7 @@ struct Grid {
 inline int clamp_floor(double v, int lo, int hi) {
     // floor(v) clamped to [lo, hi], evaluated without overflowing int.
     double f = std::floor(v);
-    if (f < lo) return lo;
+    if (!(f >= lo)) return lo;  // also maps NaN to lo
     if (f > hi) return hi;
     return static_cast<int>(f);
 }

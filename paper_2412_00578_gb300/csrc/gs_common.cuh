@@ -1,0 +1,151 @@
+// Internal definitions shared by the library's translation units.
+//
+// Floating-point contract: the library is compiled with -fmad=false, IEEE
+// division and square root, and without flush-to-zero, so every float
+// operation rounds once unless written as fmaf().  The per-Gaussian values
+// that decide tile membership (projected mean, conic, t, depth) and the
+// per-pixel blend are evaluated in a fixed operation order, so results are
+// reproducible bit for bit by any implementation that follows the same order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+constexpr int kMaxTile = 32;
+
+// ---------------------------------------------------------------- status words
+// scratch layout starts with these words (device):
+//   [0] key total K, low 32 bits   [1] K high bits   [2] GS_FLAG_* bits
+constexpr int kStatusWords = 16;
+
+struct FrameView {
+    int64_t ncap, kcap;
+    int width, height, tile, gx, gy;
+    float4* p0;  // u, v, opacity, depth
+    float4* p1;  // a, b, c, t
+    float4* p2;  // r, g, b, radius bits
+    int32_t* counts;
+    uint64_t* keys0;
+    uint64_t* keys1;
+    uint32_t* vals0;
+    uint32_t* vals1;
+    uint2* ranges;
+    float* image;
+    float* final_T;
+    uint32_t* last;
+    uint32_t* status;
+    long long* scan_partials;  // one per scan block + 1
+    uint32_t* sort_hist;       // [kMaxPasses][256]
+    uint32_t* sort_ticket;     // [kMaxPasses]
+    uint32_t* sort_lookback;   // [2][sort_partitions][256] look-back words, see sort.cu
+    int64_t sort_partitions;   // partitions the look-back table holds
+};
+
+// ---------------------------------------------------------------- scan / sort geometry
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;  // counts per thread
+constexpr int kScanBlock = kScanThreads * kScanItems;
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortPartition = kSortThreads * kSortItems;  // keys per onesweep partition
+constexpr int kMaxPasses = 8;
+
+// ---------------------------------------------------------------- elementary functions
+// Natural logarithm: frexp range reduction to m in [sqrt(1/2), sqrt(2)),
+// log x = e ln2 + 2 atanh(s), s = (m-1)/(m+1), atanh series through s^11/11;
+// ln2 split into a 15-bit head (exact products with the exponent) and a tail.
+__device__ __forceinline__ float gs_logf(float x) {
+    if (isnan(x)) return x;
+    if (!(x > 0.0f)) return -INFINITY;
+    if (isinf(x)) return x;
+    int e;
+    float m = frexpf(x, &e);
+    if (m < 0.70710677f) {
+        m = m * 2.0f;
+        e = e - 1;
+    }
+    const float s = (m - 1.0f) / (m + 1.0f);
+    const float s2 = s * s;
+    float p = 1.0f / 11.0f;
+    p = fmaf(p, s2, 1.0f / 9.0f);
+    p = fmaf(p, s2, 1.0f / 7.0f);
+    p = fmaf(p, s2, 1.0f / 5.0f);
+    p = fmaf(p, s2, 1.0f / 3.0f);
+    p = fmaf(p, s2, 1.0f);
+    const float lm = (2.0f * s) * p;
+    const float fe = (float)e;
+    return fmaf(fe, 0.693145751953125f, fmaf(fe, 1.42860682030941723e-06f, lm));
+}
+
+// Exponential: x = k ln2 + r (Cody-Waite, same ln2 split), e^r by its Taylor
+// polynomial to degree 7 (Horner), scaled by 2^k.
+__device__ __forceinline__ float gs_expf(float x) {
+    if (isnan(x)) return x;
+    if (x < -104.0f) return 0.0f;
+    if (x > 89.0f) return INFINITY;
+    const float k = rintf(x * 1.44269502f);
+    float r = fmaf(-k, 0.693145751953125f, x);
+    r = fmaf(-k, 1.42860682030941723e-06f, r);
+    float p = 1.0f / 5040.0f;
+    p = fmaf(p, r, 1.0f / 720.0f);
+    p = fmaf(p, r, 1.0f / 120.0f);
+    p = fmaf(p, r, 1.0f / 24.0f);
+    p = fmaf(p, r, 1.0f / 6.0f);
+    p = fmaf(p, r, 0.5f);
+    p = fmaf(p, r, 1.0f);
+    p = fmaf(p, r, 1.0f);
+    return ldexpf(p, (int)k);
+}
+
+// floor(x) as an int clamped to [lo, hi], safe for any finite or infinite x.
+__device__ __forceinline__ int floor_clamp(float x, int lo, int hi) {
+    const float f = floorf(x);
+    if (!(f >= (float)lo)) return lo;
+    if (f > (float)hi) return hi;
+    return (int)f;
+}
+
+// ---------------------------------------------------------------- ptx helpers
+__device__ __forceinline__ uint32_t ld_relaxed_gpu(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_gpu(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+}  // namespace gs
+
+// ---------------------------------------------------------------- context
+struct gs_context {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    int64_t launches = 0;
+    char err[512] = {0};
+};
+
+namespace gs {
+// host helpers (api.cu)
+gs_status set_error(gs_context* ctx, gs_status st, const char* fmt, ...);
+gs_status check_launch(gs_context* ctx, const char* what);
+bool make_view(gs_context* ctx, const gs_frame* f, FrameView* v);
+int sort_tile_bits(int tiles);
+void sort_plan(int tiles, int* passes, int* digit_bits);
+int64_t sort_partitions_for(int64_t kcap);
+int64_t scan_blocks_for(int64_t n);
+
+// launchers (one per translation unit); all enqueue on ctx->stream
+gs_status launch_preprocess(gs_context* ctx, const gs_scene* s, const gs_camera* cam, const gs_raster_cfg* cfg,
+                            const FrameView& v);
+gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v);
+gs_status launch_sort(gs_context* ctx, const FrameView& v);
+gs_status launch_ranges(gs_context* ctx, const FrameView& v);
+gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v);
+}  // namespace gs

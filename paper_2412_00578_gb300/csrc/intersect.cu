@@ -1,0 +1,207 @@
+// InclusiveSum + duplicateWithKeys (Sec. 3.2.2).
+//
+// Three launches:
+//   scan_reduce  each block sums 4096 tile counts (int64 partial per block);
+//   scan_top     one block turns the partials into exclusive block offsets,
+//                stores the key total K in the frame status and flags a
+//                capacity overflow;
+//   emit         each block re-reads its 4096 counts, scans them in shared
+//                memory (so per-Gaussian offsets are never stored in HBM),
+//                and every Gaussian with tiles recomputes its tile set with
+//                the same localization function the count used and writes
+//                its (tile << 32 | depth bits, index) pairs at its offset.
+#include "tiles.cuh"
+
+namespace gs {
+namespace {
+
+__device__ __forceinline__ long long warp_incl_scan(long long v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// Exclusive scan across a 256-thread block; returns the thread's exclusive
+// prefix and writes the block total to *total.
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* s_warp, long long* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long inc = warp_incl_scan(v, lane);
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+        w = warp_incl_scan(w, lane);
+        if (lane < (int)(blockDim.x >> 5)) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const long long before = warp > 0 ? s_warp[warp - 1] : 0;
+    *total = s_warp[(blockDim.x >> 5) - 1];
+    return before + inc - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const int32_t* __restrict__ counts, int64_t n,
+                                                                   long long* __restrict__ partials) {
+    __shared__ long long s_warp[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+    long long sum = 0;
+#pragma unroll 4
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        if (i < n) sum += counts[i];
+    }
+    long long total;
+    block_excl_scan(sum, s_warp, &total);
+    if (threadIdx.x == 0) partials[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) scan_top_kernel(long long* __restrict__ partials, int64_t nblocks,
+                                                        int64_t kcap, uint32_t* __restrict__ status) {
+    __shared__ long long s_warp[32];
+    __shared__ long long s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < nblocks; b0 += blockDim.x) {
+        const int64_t b = b0 + threadIdx.x;
+        const long long v = b < nblocks ? partials[b] : 0;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const long long inc = warp_incl_scan(v, lane);
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            long long w = s_warp[lane];
+            w = warp_incl_scan(w, lane);
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const long long excl = (warp > 0 ? s_warp[warp - 1] : 0) + inc - v;
+        const long long carry = s_carry;
+        if (b < nblocks) partials[b] = carry + excl;
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry = carry + s_warp[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const long long K = s_carry;
+        status[0] = (uint32_t)(K & 0xffffffffll);
+        status[1] = (uint32_t)(K >> 32);
+        if (K > kcap) atomicOr(status + 2, GS_FLAG_CAPACITY);
+    }
+}
+
+struct EmitArgs {
+    const int32_t* counts;
+    const long long* partials;  // exclusive offset of each scan block
+    const float4* p0;
+    const float4* p1;
+    const float4* p2;
+    const uint32_t* status;
+    uint64_t* keys;
+    uint32_t* vals;
+    int64_t n;
+    int mode;
+    Grid grid;
+};
+
+struct KeyWriter {
+    uint64_t* keys;
+    uint32_t* vals;
+    long long pos;
+    long long end;  // one past this Gaussian's last slot (offset + counted tiles)
+    uint32_t depth_bits;
+    uint32_t id;
+    int gx;
+    __device__ __forceinline__ void put(uint32_t tile) {
+        if (pos < end) {  // the recount always equals the count; never write past it regardless
+            keys[pos] = ((uint64_t)tile << 32) | depth_bits;
+            vals[pos] = id;
+        }
+        ++pos;
+    }
+    // AccuTile line callback: rows -> line k is tile row ty = k, span over tx;
+    // columns -> line k is tile column tx = k, span over ty.
+    __device__ __forceinline__ void operator()(int k, int jmin, int jmax, bool rows) {
+        if (rows) {
+            for (int j = jmin; j <= jmax; ++j) put((uint32_t)(k * gx + j));
+        } else {
+            for (int j = jmin; j <= jmax; ++j) put((uint32_t)(j * gx + k));
+        }
+    }
+};
+
+__global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
+    __shared__ long long s_warp[32];
+    if (A.status[2] & GS_FLAG_CAPACITY) return;  // keys do not fit: emit nothing
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+    int c[kScanItems];
+    long long sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + k;
+        c[k] = i < A.n ? A.counts[i] : 0;
+        sum += c[k];
+    }
+    long long total;
+    long long off = block_excl_scan(sum, s_warp, &total) + A.partials[blockIdx.x];
+#pragma unroll 1
+    for (int k = 0; k < kScanItems; ++k) {
+        if (c[k] == 0) continue;
+        const int64_t i = base + k;
+        const float4 q0 = A.p0[i];
+        KeyWriter W{A.keys, A.vals, off, off + c[k], __float_as_uint(q0.w), (uint32_t)i, A.grid.gx};
+        if (A.mode == GS_MODE_3SIGMA) {
+            Rect R;
+            if (sigma3_rect(q0.x, q0.y, __float_as_int(A.p2[i].w), A.grid, R))
+                for (int ty = R.y0; ty <= R.y1; ++ty)
+                    for (int tx = R.x0; tx <= R.x1; ++tx) W.put((uint32_t)(ty * A.grid.gx + tx));
+        } else {
+            const float4 q1 = A.p1[i];
+            const Ellipse E{q0.x, q0.y, q1.x, q1.y, q1.z, q1.w};
+            Snug S;
+            if (snugbox(E, A.grid, S)) {
+                if (A.mode == GS_MODE_SNUGBOX) {
+                    for (int ty = S.R.y0; ty <= S.R.y1; ++ty)
+                        for (int tx = S.R.x0; tx <= S.R.x1; ++tx) W.put((uint32_t)(ty * A.grid.gx + tx));
+                } else {
+                    accutile_sweep(E, S, A.grid, W);
+                }
+            }
+        }
+        off += c[k];
+    }
+}
+
+}  // namespace
+
+gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v) {
+    const int64_t nb = scan_blocks_for(v.ncap);
+    if (cudaMemsetAsync(v.status, 0, kStatusWords * sizeof(uint32_t), ctx->stream) != cudaSuccess)
+        return set_error(ctx, GS_ERR_CUDA, "intersect: cudaMemsetAsync(status) failed");
+    if (nb > 0) {
+        scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(v.counts, v.ncap, v.scan_partials);
+        ctx->launches += 1;
+    }
+    scan_top_kernel<<<1, 1024, 0, ctx->stream>>>(v.scan_partials, nb, v.kcap, v.status);
+    ctx->launches += 1;
+    if (nb > 0) {
+        EmitArgs A;
+        A.counts = v.counts;
+        A.partials = v.scan_partials;
+        A.p0 = v.p0;
+        A.p1 = v.p1;
+        A.p2 = v.p2;
+        A.status = v.status;
+        A.keys = v.keys0;
+        A.vals = v.vals0;
+        A.n = v.ncap;
+        A.mode = cfg->mode;
+        A.grid = Grid{(float)v.tile, v.gx, v.gy};
+        emit_kernel<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(A);
+        ctx->launches += 1;
+    }
+    return check_launch(ctx, "intersect");
+}
+
+}  // namespace gs

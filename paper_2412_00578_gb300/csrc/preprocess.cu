@@ -1,0 +1,227 @@
+// preprocess (Sec. 3.2.1): one thread per Gaussian.
+//
+// Reads the planar parameter arrays with coalesced 4-byte loads (a warp reads
+// 128 contiguous bytes of each plane), computes the 2D state and the tile
+// count of the requested mode, and only for Gaussians that touch at least one
+// tile reads the SH coefficients (192 of the 236 bytes of a Gaussian) and
+// writes the 48-byte 2D state.  Gaussians that are culled or off-screen cost
+// their 40 bytes of geometry and opacity plus a 4-byte count.
+#include "tiles.cuh"
+
+namespace gs {
+namespace {
+
+struct CamK {
+    float fx, fy, cx, cy, limx, limy, near_z;
+    float V[12];
+    float campos[3];
+};
+
+struct PreArgs {
+    const float* means;
+    const float* scales;
+    const float* rots;
+    const float* opac;
+    const float* sh;
+    int64_t n;      // Gaussians in the scene
+    int64_t ncap;   // counts written for [0, ncap)
+    int sh_coeffs;  // (degree + 1)^2
+    int mode;
+    Grid grid;
+    CamK cam;
+    float4* p0;
+    float4* p1;
+    float4* p2;
+    int32_t* counts;
+};
+
+// Real SH normalisation constants, from their closed forms:
+// 1/(2 sqrt(pi)), sqrt(3/(4pi)), sqrt(15/(4pi)), sqrt(5/(16pi)), sqrt(15/(16pi)),
+// sqrt(35/(32pi)), sqrt(105/(4pi)), sqrt(21/(32pi)), sqrt(7/(16pi)), sqrt(105/(16pi)).
+constexpr float kC0 = 0.28209479177387814f;
+constexpr float kC1 = 0.4886025119029199f;
+constexpr float kC2a = 1.0925484305920792f;
+constexpr float kC2c = 0.31539156525252005f;
+constexpr float kC2e = 0.5462742152960396f;
+constexpr float kC3a = 0.5900435899266435f;
+constexpr float kC3b = 2.890611442640554f;
+constexpr float kC3c = 0.4570457994644658f;
+constexpr float kC3d = 0.3731763325901154f;
+constexpr float kC3f = 1.445305721320277f;
+
+__device__ __forceinline__ void sh_basis16(float x, float y, float z, float Y[16]) {
+    Y[0] = kC0;
+    Y[1] = (-kC1) * y;
+    Y[2] = kC1 * z;
+    Y[3] = (-kC1) * x;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    const float xy = x * y, yz = y * z, xz = x * z;
+    Y[4] = kC2a * xy;
+    Y[5] = (-kC2a) * yz;
+    Y[6] = kC2c * ((2.0f * zz - xx) - yy);
+    Y[7] = (-kC2a) * xz;
+    Y[8] = kC2e * (xx - yy);
+    Y[9] = ((-kC3a) * y) * (3.0f * xx - yy);
+    Y[10] = (kC3b * xy) * z;
+    Y[11] = ((-kC3c) * y) * ((4.0f * zz - xx) - yy);
+    Y[12] = (kC3d * z) * ((2.0f * zz - 3.0f * xx) - 3.0f * yy);
+    Y[13] = ((-kC3c) * x) * ((4.0f * zz - xx) - yy);
+    Y[14] = (kC3f * z) * (xx - yy);
+    Y[15] = ((-kC3a) * x) * (xx - 3.0f * yy);
+}
+
+__global__ void __launch_bounds__(256) preprocess_kernel(const PreArgs A) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.ncap) return;
+    int count = 0;
+    if (i < A.n) {
+        const int64_t n = A.n;
+        const float mx = __ldg(A.means + i), my = __ldg(A.means + n + i), mz = __ldg(A.means + 2 * n + i);
+        const float s0 = __ldg(A.scales + i), s1 = __ldg(A.scales + n + i), s2 = __ldg(A.scales + 2 * n + i);
+        const float qw = __ldg(A.rots + i), qx = __ldg(A.rots + n + i), qy = __ldg(A.rots + 2 * n + i),
+                    qz = __ldg(A.rots + 3 * n + i);
+        const float sigma = __ldg(A.opac + i);
+        const CamK& C = A.cam;
+        bool ok = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(s0) && isfinite(s1) && isfinite(s2) &&
+                  isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) && isfinite(sigma);
+        // view transform
+        const float px = ((C.V[0] * mx + C.V[1] * my) + C.V[2] * mz) + C.V[3];
+        const float py = ((C.V[4] * mx + C.V[5] * my) + C.V[6] * mz) + C.V[7];
+        const float pz = ((C.V[8] * mx + C.V[9] * my) + C.V[10] * mz) + C.V[11];
+        ok = ok && (pz > C.near_z);
+        const float n2 = ((qw * qw + qx * qx) + qy * qy) + qz * qz;
+        ok = ok && (n2 > 0.0f);
+        if (ok) {
+            const float xz = px / pz;
+            const float yz = py / pz;
+            const float u = C.fx * xz + C.cx;
+            const float v = C.fy * yz + C.cy;
+            // rotation from the normalised quaternion
+            const float nq = sqrtf(n2);
+            const float w = qw / nq, x = qx / nq, y = qy / nq, z = qz / nq;
+            float R[9];
+            R[0] = 1.0f - 2.0f * (y * y + z * z);
+            R[1] = 2.0f * (x * y - w * z);
+            R[2] = 2.0f * (x * z + w * y);
+            R[3] = 2.0f * (x * y + w * z);
+            R[4] = 1.0f - 2.0f * (x * x + z * z);
+            R[5] = 2.0f * (y * z - w * x);
+            R[6] = 2.0f * (x * z - w * y);
+            R[7] = 2.0f * (y * z + w * x);
+            R[8] = 1.0f - 2.0f * (x * x + y * y);
+            // Sigma3D = (R S)(R S)^T
+            float M[9];
+            const float sc[3] = {s0, s1, s2};
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) M[3 * r + k] = R[3 * r + k] * sc[k];
+            float S3[9];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    S3[3 * r + c] = (M[3 * r] * M[3 * c] + M[3 * r + 1] * M[3 * c + 1]) + M[3 * r + 2] * M[3 * c + 2];
+            // Jacobian at the clamped mean
+            const float tx = fminf(C.limx, fmaxf(-C.limx, xz)) * pz;
+            const float ty = fminf(C.limy, fmaxf(-C.limy, yz)) * pz;
+            const float zz = pz * pz;
+            const float j00 = C.fx / pz;
+            const float j02 = -((C.fx * tx) / zz);
+            const float j11 = C.fy / pz;
+            const float j12 = -((C.fy * ty) / zz);
+            float T0[3], T1[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                T0[k] = j00 * C.V[k] + j02 * C.V[8 + k];
+                T1[k] = j11 * C.V[4 + k] + j12 * C.V[8 + k];
+            }
+            float U0[3], U1[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                U0[c] = (T0[0] * S3[c] + T0[1] * S3[3 + c]) + T0[2] * S3[6 + c];
+                U1[c] = (T1[0] * S3[c] + T1[1] * S3[3 + c]) + T1[2] * S3[6 + c];
+            }
+            const float c00 = (U0[0] * T0[0] + U0[1] * T0[1]) + U0[2] * T0[2];
+            const float c01 = (U0[0] * T1[0] + U0[1] * T1[1]) + U0[2] * T1[2];
+            const float c11 = (U1[0] * T1[0] + U1[1] * T1[1]) + U1[2] * T1[2];
+            const float sxx = c00 + 0.3f;
+            const float syy = c11 + 0.3f;
+            const float sxy = c01;
+            const float det = sxx * syy - sxy * sxy;
+            if (det > 0.0f) {
+                const float a = syy / det;
+                const float b = (-sxy) / det;
+                const float c = sxx / det;
+                if (isfinite(u) && isfinite(v) && isfinite(a) && isfinite(b) && isfinite(c)) {
+                    const float t = 2.0f * gs_logf(255.0f * sigma);
+                    const float mid = 0.5f * (sxx + syy);
+                    const float disc = fmaxf(0.1f, mid * mid - det);
+                    const float l1 = mid + sqrtf(disc);
+                    const float rad = ceilf(3.0f * sqrtf(l1));
+                    const int radius = (rad >= 0.0f && rad < 1073741824.0f) ? (int)rad : (1 << 30);
+                    const Ellipse E{u, v, a, b, c, t};
+                    count = tile_count(A.mode, E, radius, A.grid);
+                    if (count > 0) {
+                        // SH colour, read only for Gaussians that touch a tile
+                        const float d0 = mx - C.campos[0], d1 = my - C.campos[1], d2 = mz - C.campos[2];
+                        const float len = sqrtf((d0 * d0 + d1 * d1) + d2 * d2);
+                        float Y[16];
+                        sh_basis16(d0 / len, d1 / len, d2 / len, Y);
+                        float rgb[3];
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) {
+                            float acc = Y[0] * __ldg(A.sh + (int64_t)ch * n + i);
+                            for (int k = 1; k < A.sh_coeffs; ++k)
+                                acc = acc + Y[k] * __ldg(A.sh + (int64_t)(k * 3 + ch) * n + i);
+                            acc = acc + 0.5f;
+                            rgb[ch] = acc < 0.0f ? 0.0f : acc;
+                        }
+                        A.p0[i] = make_float4(u, v, sigma, pz);
+                        A.p1[i] = make_float4(a, b, c, t);
+                        A.p2[i] = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(radius));
+                    }
+                }
+            }
+        }
+    }
+    A.counts[i] = count;
+}
+
+}  // namespace
+
+gs_status launch_preprocess(gs_context* ctx, const gs_scene* s, const gs_camera* cam, const gs_raster_cfg* cfg,
+                            const FrameView& v) {
+    PreArgs A;
+    A.means = s->means;
+    A.scales = s->scales;
+    A.rots = s->rotations;
+    A.opac = s->opacities;
+    A.sh = s->sh;
+    A.n = s->n;
+    A.ncap = v.ncap;
+    A.sh_coeffs = (s->sh_degree + 1) * (s->sh_degree + 1);
+    A.mode = cfg->mode;
+    A.grid = Grid{(float)v.tile, v.gx, v.gy};
+    A.cam.fx = cam->fx;
+    A.cam.fy = cam->fy;
+    A.cam.cx = cam->cx;
+    A.cam.cy = cam->cy;
+    A.cam.limx = 1.3f * cam->tan_fovx;
+    A.cam.limy = 1.3f * cam->tan_fovy;
+    A.cam.near_z = cam->near_z;
+    for (int k = 0; k < 12; ++k) A.cam.V[k] = cam->viewmat[k];
+    for (int k = 0; k < 3; ++k) A.cam.campos[k] = cam->campos[k];
+    A.p0 = v.p0;
+    A.p1 = v.p1;
+    A.p2 = v.p2;
+    A.counts = v.counts;
+    if (v.ncap == 0) return GS_OK;
+    const int threads = 256;
+    const int64_t blocks = (v.ncap + threads - 1) / threads;
+    preprocess_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(A);
+    ctx->launches += 1;
+    return check_launch(ctx, "preprocess");
+}
+
+}  // namespace gs

@@ -1,0 +1,279 @@
+// RadixSort (Sec. 3.2.2): stable least-significant-digit radix sort of the
+// (key, value) pairs, onesweep style.
+//
+//   sort_hist   one read of the keys builds the digit histograms of every
+//               pass at once (shared-memory counters, one global atomic per
+//               bin per block) and clears the first look-back table.
+//   sort_pass   one launch per digit.  Each block takes a 4096-key partition
+//               by atomic ticket (so partitions are processed in launch
+//               order and every predecessor is already resident), ranks its
+//               keys by digit stably (warp match + per-warp counters),
+//               publishes its per-digit counts, and resolves its global
+//               offsets by decoupled look-back over its predecessors'
+//               published counts.  Keys are staged in shared memory in digit
+//               order so each digit's run is written to HBM contiguously.
+//               Every wait on a predecessor is bounded; when the bound is
+//               reached the block records GS_FLAG_TIMEOUT and proceeds, so
+//               no kernel can hang.
+//
+// Bits sorted: the 32 depth bits plus ceil(log2(tiles)) tile bits, split
+// into an even number of passes so the result lands back in buffer 0.
+#include <algorithm>
+
+#include "gs_common.cuh"
+
+namespace gs {
+namespace {
+
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagPrefix = 2u << 30;
+constexpr uint32_t kCountMask = (1u << 30) - 1;
+constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kNoDigit = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t frame_keys(const uint32_t* status) {
+    return (status[2] & GS_FLAG_CAPACITY) ? 0u : status[0];
+}
+
+struct HistArgs {
+    const uint64_t* keys;
+    const uint32_t* status;
+    uint32_t* hist;        // [passes][256]
+    uint32_t* lookback0;   // first pass's table, cleared here
+    int passes, dbits;
+};
+
+__global__ void __launch_bounds__(256) sort_hist_kernel(const HistArgs A) {
+    __shared__ uint32_t sh[kMaxPasses * 256];
+    for (int i = threadIdx.x; i < A.passes * 256; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const uint32_t K = frame_keys(A.status);
+    const uint32_t mask = (1u << A.dbits) - 1u;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += stride) {
+        const uint64_t key = A.keys[i];
+        for (int p = 0; p < A.passes; ++p) atomicAdd(&sh[p * 256 + (uint32_t)((key >> (p * A.dbits)) & mask)], 1u);
+    }
+    // clear the look-back words of the partitions the first pass will use
+    const uint32_t words = ((K + kSortPartition - 1) / kSortPartition) * 256u;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) A.lookback0[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < A.passes * 256; i += blockDim.x)
+        if (sh[i]) atomicAdd(&A.hist[i], sh[i]);
+}
+
+// Exclusive scan of one value per thread over a 256-thread block.
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < 8 ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < 8) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t r = (warp > 0 ? s_warp[warp - 1] : 0u) + inc - v;
+    __syncthreads();
+    return r;
+}
+
+struct PassArgs {
+    const uint64_t* kin;
+    const uint32_t* vin;
+    uint64_t* kout;
+    uint32_t* vout;
+    uint32_t* status;
+    const uint32_t* hist;   // this pass's 256 digit totals
+    uint32_t* lookback;     // this pass's table [partitions][256]
+    uint32_t* lookback_next;// next pass's table: this block clears its own row
+    uint32_t* ticket;
+    int shift, dbits;
+};
+
+struct PassSmem {
+    uint64_t keys[kSortPartition];
+    uint32_t vals[kSortPartition];
+    uint32_t wcnt[kSortThreads / 32][256];
+    uint32_t boff[256];
+    uint32_t gbase[256];
+    uint32_t warp_tmp[32];
+    uint32_t part;
+};
+
+__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(const PassArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PassSmem& S = *reinterpret_cast<PassSmem*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) S.part = atomicAdd(A.ticket, 1u);
+    for (int i = tid; i < (kSortThreads / 32) * 256; i += kSortThreads) (&S.wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t K = frame_keys(A.status);
+    const uint32_t part = S.part;
+    const uint32_t nparts = (K + kSortPartition - 1) / kSortPartition;
+    if (part >= nparts) return;
+    const uint32_t base = part * kSortPartition;
+    const uint32_t mask = (1u << A.dbits) - 1u;
+
+    // Load: warp w owns keys [base + 512 w, base + 512 (w+1)); round r reads
+    // 32 consecutive keys, so (warp, round, lane) order is input order.
+    uint64_t key[kSortItems];
+    uint32_t val[kSortItems];
+    uint32_t rank[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t idx = base + warp * (kSortItems * 32) + r * 32 + lane;
+        const bool ok = idx < K;
+        key[r] = ok ? A.kin[idx] : 0ull;
+        val[r] = ok ? A.vin[idx] : 0u;
+    }
+    // Stable ranking within the warp, round by round.
+    const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t idx = base + warp * (kSortItems * 32) + r * 32 + lane;
+        const uint32_t d = idx < K ? (uint32_t)((key[r] >> A.shift) & mask) : kNoDigit;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = 0;
+        if (d != kNoDigit) before = S.wcnt[warp][d];
+        rank[r] = before + __popc(peers & lt_mask);
+        __syncwarp();
+        if (d != kNoDigit && (peers & lt_mask) == 0) S.wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // Per digit (thread t <-> digit t): warp-exclusive offsets and block total.
+    const uint32_t t = tid;
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) {
+        const uint32_t c = S.wcnt[w][t];
+        S.wcnt[w][t] = tot;
+        tot += c;
+    }
+    uint32_t* my = A.lookback + (size_t)part * 256 + t;
+    st_relaxed_gpu(my, (part == 0 ? kFlagPrefix : kFlagAgg) | tot);
+    // clear this partition's row of the next pass's table (that table's last
+    // user was the previous pass, which has completed)
+    if (A.lookback_next) A.lookback_next[(size_t)part * 256 + t] = 0;
+    const uint32_t boff = block_excl_scan_u32(tot, S.warp_tmp);
+    const uint32_t dstart = block_excl_scan_u32(A.hist[t], S.warp_tmp);
+    uint32_t prefix = 0;
+    if (part > 0) {
+        int64_t j = (int64_t)part - 1;
+        uint32_t spins = 0;
+        while (j >= 0) {
+            const uint32_t w = ld_relaxed_gpu(A.lookback + (size_t)j * 256 + t);
+            const uint32_t flag = w & ~kCountMask;
+            if (flag == 0) {
+                if (++spins > kSpinLimit) {
+                    atomicOr(A.status + 2, GS_FLAG_TIMEOUT);
+                    break;
+                }
+                __nanosleep(32);
+                continue;
+            }
+            prefix += w & kCountMask;
+            if (flag == kFlagPrefix) break;
+            --j;
+        }
+        st_relaxed_gpu(my, kFlagPrefix | (prefix + tot));
+    }
+    S.boff[t] = boff;
+    S.gbase[t] = dstart + prefix - boff;  // modular: gbase + staging index = output index
+    __syncthreads();
+    // Stage in digit order.
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t idx = base + warp * (kSortItems * 32) + r * 32 + lane;
+        if (idx < K) {
+            const uint32_t d = (uint32_t)((key[r] >> A.shift) & mask);
+            const uint32_t pos = S.boff[d] + S.wcnt[warp][d] + rank[r];
+            S.keys[pos] = key[r];
+            S.vals[pos] = val[r];
+        }
+    }
+    __syncthreads();
+    const uint32_t nvalid = min((uint32_t)kSortPartition, K - base);
+    for (uint32_t i = tid; i < nvalid; i += kSortThreads) {
+        const uint64_t k = S.keys[i];
+        const uint32_t d = (uint32_t)((k >> A.shift) & mask);
+        const uint32_t o = S.gbase[d] + i;
+        if (o < K) {  // always true unless a look-back wait timed out (flagged above)
+            A.kout[o] = k;
+            A.vout[o] = S.vals[i];
+        }
+    }
+}
+
+}  // namespace
+
+int sort_tile_bits(int tiles) {
+    int b = 0;
+    while ((1ll << b) < (long long)tiles) ++b;
+    return b;
+}
+
+void sort_plan(int tiles, int* passes, int* digit_bits) {
+    const int bits = 32 + sort_tile_bits(tiles);
+    const int p = 2 * ((bits + 15) / 16);
+    *passes = p;
+    *digit_bits = (bits + p - 1) / p;
+}
+
+int64_t sort_partitions_for(int64_t kcap) { return (kcap + kSortPartition - 1) / kSortPartition; }
+
+gs_status launch_sort(gs_context* ctx, const FrameView& v) {
+    int passes, dbits;
+    sort_plan(v.gx * v.gy, &passes, &dbits);
+    static bool attr_done[64] = {false};
+    if (!attr_done[ctx->device & 63]) {
+        if (cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(PassSmem)) != cudaSuccess)
+            return set_error(ctx, GS_ERR_CUDA, "sort: cannot raise dynamic shared memory to %d bytes",
+                             (int)sizeof(PassSmem));
+        attr_done[ctx->device & 63] = true;
+    }
+    // histograms and tickets start at zero
+    if (cudaMemsetAsync(v.sort_hist, 0, (kMaxPasses * 256 + kMaxPasses) * sizeof(uint32_t), ctx->stream) !=
+        cudaSuccess)
+        return set_error(ctx, GS_ERR_CUDA, "sort: cudaMemsetAsync failed");
+    if (v.kcap == 0) return GS_OK;
+    const int64_t parts = sort_partitions_for(v.kcap);
+    const size_t table = (size_t)v.sort_partitions * 256;
+    HistArgs H{v.keys0, v.status, v.sort_hist, v.sort_lookback, passes, dbits};
+    int hblocks = (int)std::min<int64_t>((v.kcap + 2047) / 2048, (int64_t)ctx->num_sms * 8);
+    if (hblocks < 1) hblocks = 1;
+    sort_hist_kernel<<<hblocks, 256, 0, ctx->stream>>>(H);
+    ctx->launches += 1;
+    for (int p = 0; p < passes; ++p) {
+        PassArgs A;
+        const bool even = (p % 2) == 0;
+        A.kin = even ? v.keys0 : v.keys1;
+        A.vin = even ? v.vals0 : v.vals1;
+        A.kout = even ? v.keys1 : v.keys0;
+        A.vout = even ? v.vals1 : v.vals0;
+        A.status = v.status;
+        A.hist = v.sort_hist + p * 256;
+        A.lookback = v.sort_lookback + (even ? 0 : table);
+        A.lookback_next = (p + 1 < passes) ? v.sort_lookback + (even ? table : 0) : nullptr;
+        A.ticket = v.sort_hist + kMaxPasses * 256 + p;
+        A.shift = p * dbits;
+        A.dbits = dbits;
+        sort_pass_kernel<<<(unsigned)parts, kSortThreads, sizeof(PassSmem), ctx->stream>>>(A);
+        ctx->launches += 1;
+    }
+    return check_launch(ctx, "sort");
+}
+
+}  // namespace gs

@@ -1,0 +1,173 @@
+// Gaussian-to-tile localization: the 3D-GS 3-sigma square (Eq. radius),
+// SnugBox (Sec. 4.1.1) and AccuTile (Sec. 4.1.2, Algorithm 1), as device
+// functions shared by the counting pass (preprocess) and the emitting pass
+// (duplicateWithKeys).  Both passes call the same function, so the count
+// always equals the number of keys emitted.
+#pragma once
+
+#include "gs_common.cuh"
+
+namespace gs {
+
+// 2D Gaussian in the form the localization needs: centre (u, v), conic
+// [[a b][b c]] and threshold t = 2 log(255 sigma) so that alpha >= 1/255
+// <=> q = a xd^2 + 2 b xd yd + c yd^2 <= t (Eq. simplified_ellipse).
+struct Ellipse {
+    float u, v, a, b, c, t;
+};
+
+struct Grid {
+    float T;      // tile edge, pixels
+    int gx, gy;   // tiles per row, per column
+};
+
+// 3D-GS rectangle: min = trunc((mu - r)/T), max (exclusive) =
+// trunc((mu + r + T - 1)/T), both clamped to [0, G].
+__device__ __forceinline__ int trunc_clamp(float x, int G) {
+    if (!(x > 0.0f)) return 0;
+    if (x >= (float)G) return G;
+    return (int)x;
+}
+
+struct Rect {
+    int x0, x1, y0, y1;  // inclusive bounds
+};
+
+__device__ __forceinline__ bool sigma3_rect(float u, float v, int radius, const Grid& g, Rect& R) {
+    const float r = (float)radius;
+    R.x0 = trunc_clamp((u - r) / g.T, g.gx);
+    R.x1 = trunc_clamp(((u + r) + (g.T - 1.0f)) / g.T, g.gx) - 1;
+    R.y0 = trunc_clamp((v - r) / g.T, g.gy);
+    R.y1 = trunc_clamp(((v + r) + (g.T - 1.0f)) / g.T, g.gy) - 1;
+    return R.x1 >= R.x0 && R.y1 >= R.y0;
+}
+
+// SnugBox: half-extents hx = sqrt(t c / D), hy = sqrt(t a / D), D = a c - b^2
+// (Eqs. ellipse_intersect + bbox_args), tile rectangle floor(edge / T)
+// clamped to the grid, empty if the box misses the grid.
+struct Snug {
+    float D, hx, hy, x0, x1, y0, y1;
+    Rect R;
+};
+
+__device__ __forceinline__ bool snugbox(const Ellipse& E, const Grid& g, Snug& S) {
+    if (!(E.t > 0.0f)) return false;
+    const float D = E.a * E.c - E.b * E.b;
+    if (!(D > 0.0f)) return false;
+    S.D = D;
+    S.hx = sqrtf((E.t * E.c) / D);
+    S.hy = sqrtf((E.t * E.a) / D);
+    S.x0 = E.u - S.hx;
+    S.x1 = E.u + S.hx;
+    S.y0 = E.v - S.hy;
+    S.y1 = E.v + S.hy;
+    if (!(S.x1 >= 0.0f) || !(S.y1 >= 0.0f) || !(S.x0 < (float)g.gx * g.T) || !(S.y0 < (float)g.gy * g.T))
+        return false;
+    S.R.x0 = floor_clamp(S.x0 / g.T, 0, g.gx - 1);
+    S.R.x1 = floor_clamp(S.x1 / g.T, 0, g.gx - 1);
+    S.R.y0 = floor_clamp(S.y0 / g.T, 0, g.gy - 1);
+    S.R.y1 = floor_clamp(S.y1 / g.T, 0, g.gy - 1);
+    return true;
+}
+
+// AccuTile sweep over the shorter side of the SnugBox tile rectangle.
+// For each swept line k (a tile row, or a tile column), the ellipse's
+// extent inside the line comes from the SnugBox extreme point when that
+// point lies inside it, otherwise from the ellipse's intersections with the
+// line's two boundaries; each boundary is intersected once and reused by the
+// next line.  emit(k, jmin, jmax, rows) is called once per non-empty line
+// with the inclusive span of tiles; returns the tile count.
+// Edge rules: a boundary is intersected only if it lies inside the SnugBox
+// span; the discriminant is clamped at 0; a line with neither an extreme
+// point nor an intersection falls back to the SnugBox edges; a line whose
+// extent lies entirely outside the rectangle's tile span contributes nothing.
+template <class Emit>
+__device__ __forceinline__ int accutile_sweep(const Ellipse& E, const Snug& S, const Grid& g, Emit&& emit) {
+    const bool rows = (S.R.y1 - S.R.y0) <= (S.R.x1 - S.R.x0);
+    const float ms = rows ? E.v : E.u;
+    const float me = rows ? E.u : E.v;
+    const float as = rows ? E.a : E.c;
+    const float cs = rows ? E.c : E.a;
+    const float s_lo = rows ? S.y0 : S.x0;
+    const float s_hi = rows ? S.y1 : S.x1;
+    const float e_lo = rows ? S.x0 : S.y0;
+    const float e_hi = rows ? S.x1 : S.y1;
+    const float h_e = rows ? S.hx : S.hy;
+    const int k0 = rows ? S.R.y0 : S.R.x0;
+    const int k1 = rows ? S.R.y1 : S.R.x1;
+    const int j0 = rows ? S.R.x0 : S.R.y0;
+    const int j1 = rows ? S.R.x1 : S.R.y1;
+    const float bc = E.b / cs;
+    const float pmin_s = ms + bc * h_e;
+    const float pmax_s = ms - bc * h_e;
+    const float at = as * E.t;
+    const float nb0 = -E.b;
+    auto isect = [&](float L, float& lo, float& hi) {
+        const float d = L - ms;
+        float disc = at - (S.D * d) * d;
+        if (disc < 0.0f) disc = 0.0f;
+        const float sq = sqrtf(disc);
+        const float nb = nb0 * d;
+        lo = me + (nb - sq) / as;
+        hi = me + (nb + sq) / as;
+    };
+    int cnt = 0;
+    float lo_l = 0.0f, lo_r = 0.0f;
+    bool have_lo = false;
+    const float Llo = (float)k0 * g.T;
+    if (Llo >= s_lo) {
+        isect(Llo, lo_l, lo_r);
+        have_lo = true;
+    }
+    for (int k = k0; k <= k1; ++k) {
+        const float rlo = (float)k * g.T;
+        const float rhi = (float)(k + 1) * g.T;
+        float hi_l = 0.0f, hi_r = 0.0f;
+        const bool have_hi = rhi <= s_hi;
+        if (have_hi) isect(rhi, hi_l, hi_r);
+        float emin, emax;
+        if (pmin_s >= rlo && pmin_s < rhi) emin = e_lo;
+        else if (have_lo && have_hi) emin = fminf(lo_l, hi_l);
+        else if (have_lo) emin = lo_l;
+        else if (have_hi) emin = hi_l;
+        else emin = e_lo;
+        if (pmax_s >= rlo && pmax_s < rhi) emax = e_hi;
+        else if (have_lo && have_hi) emax = fmaxf(lo_r, hi_r);
+        else if (have_lo) emax = lo_r;
+        else if (have_hi) emax = hi_r;
+        else emax = e_hi;
+        const float qmin = emin / g.T;
+        const float qmax = emax / g.T;
+        const float fmn = floorf(qmin);
+        const float fmx = floorf(qmax);
+        const int jmin = floor_clamp(qmin, j0, j1);
+        const int jmax = floor_clamp(qmax, j0, j1);
+        if (fmn <= (float)j1 && fmx >= (float)j0 && jmax >= jmin) {
+            cnt += jmax - jmin + 1;
+            emit(k, jmin, jmax, rows);
+        }
+        lo_l = hi_l;
+        lo_r = hi_r;
+        have_lo = have_hi;
+    }
+    return cnt;
+}
+
+struct NoEmit {
+    __device__ __forceinline__ void operator()(int, int, int, bool) const {}
+};
+
+// Tile count of one Gaussian in `mode` (0 when culled).
+__device__ __forceinline__ int tile_count(int mode, const Ellipse& E, int radius, const Grid& g) {
+    if (mode == GS_MODE_3SIGMA) {
+        Rect R;
+        if (!sigma3_rect(E.u, E.v, radius, g, R)) return 0;
+        return (R.x1 - R.x0 + 1) * (R.y1 - R.y0 + 1);
+    }
+    Snug S;
+    if (!snugbox(E, g, S)) return 0;
+    if (mode == GS_MODE_SNUGBOX) return (S.R.x1 - S.R.x0 + 1) * (S.R.y1 - S.R.y0 + 1);
+    return accutile_sweep(E, S, g, NoEmit{});
+}
+
+}  // namespace gs

@@ -1,0 +1,328 @@
+"""Python binding of the C ABI in ``include/gs.h`` (argument marshalling only).
+
+Every stage runs in the CUDA library ``_build/libgs.so``; this module only
+allocates the caller-owned device buffers with PyTorch, fills the C structs
+and checks status codes.  Importing it raises if the library has not been
+built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, c_float, c_int32, c_int64, c_uint32, c_void_p
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+MODES = {"3sigma": 0, "snugbox": 1, "accutile": 2}
+MODE_NAMES = {v: k for k, v in MODES.items()}
+FLAG_CAPACITY = 1
+FLAG_TIMEOUT = 2
+STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID", 2: "GS_ERR_OOM", 3: "GS_ERR_CAPACITY", 4: "GS_ERR_CUDA",
+                5: "GS_ERR_TIMEOUT"}
+MAX_KEYS = (1 << 30) - 1
+
+
+class GsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class GsScene(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("sh_degree", c_int32), ("means", c_void_p), ("scales", c_void_p),
+                ("rotations", c_void_p), ("opacities", c_void_p), ("sh", c_void_p)]
+
+
+class GsCamera(ctypes.Structure):
+    _fields_ = [("width", c_int32), ("height", c_int32), ("fx", c_float), ("fy", c_float), ("cx", c_float),
+                ("cy", c_float), ("tan_fovx", c_float), ("tan_fovy", c_float), ("near_z", c_float),
+                ("viewmat", c_float * 12), ("campos", c_float * 3)]
+
+
+class GsRasterCfg(ctypes.Structure):
+    _fields_ = [("tile", c_int32), ("mode", c_int32), ("bg", c_float * 3)]
+
+
+class GsFrame(ctypes.Structure):
+    _fields_ = [("n_capacity", c_int64), ("key_capacity", c_int64), ("width", c_int32), ("height", c_int32),
+                ("tile", c_int32), ("proj", c_void_p), ("counts", c_void_p), ("keys", c_void_p),
+                ("vals", c_void_p), ("ranges", c_void_p), ("image", c_void_p), ("final_T", c_void_p),
+                ("last", c_void_p), ("scratch", c_void_p)]
+
+
+class GsFrameBytes(ctypes.Structure):
+    _fields_ = [(k, c_int64) for k in ("proj", "counts", "keys", "vals", "ranges", "image", "final_T", "last",
+                                       "scratch")]
+
+
+EXPORTS = ["gs_create", "gs_destroy", "gs_set_stream", "gs_last_error", "gs_launch_count", "gs_frame_sizes",
+           "gs_preprocess", "gs_intersect", "gs_sort", "gs_tile_ranges", "gs_render", "gs_forward",
+           "gs_read_status"]
+
+_lib = None
+
+
+def load(path=None) -> ctypes.CDLL:
+    """Load libgs.so; raises if it is missing (build it with ``build.build()``)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build.LIB
+    if not p.exists():
+        raise RuntimeError(f"CUDA library {p} is not built; run paper_2412_00578_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(str(p))
+    P = c_void_p
+    L.gs_create.argtypes = [ctypes.c_int, P, POINTER(c_void_p)]
+    L.gs_destroy.argtypes = [P]
+    L.gs_destroy.restype = None
+    L.gs_set_stream.argtypes = [P, P]
+    L.gs_last_error.argtypes = [P]
+    L.gs_last_error.restype = ctypes.c_char_p
+    L.gs_launch_count.argtypes = [P]
+    L.gs_launch_count.restype = c_int64
+    L.gs_frame_sizes.argtypes = [c_int64, c_int32, c_int32, c_int32, c_int64, POINTER(GsFrameBytes)]
+    L.gs_preprocess.argtypes = [P, POINTER(GsScene), POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame)]
+    L.gs_intersect.argtypes = [P, POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame), POINTER(c_int64)]
+    for name in ("gs_sort", "gs_tile_ranges", "gs_render"):
+        getattr(L, name).argtypes = [P, POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame)]
+    L.gs_forward.argtypes = [P, POINTER(GsScene), POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame)]
+    L.gs_read_status.argtypes = [P, POINTER(GsFrame), POINTER(c_int64), POINTER(c_uint32)]
+    for name in EXPORTS:
+        getattr(L, name).restype = ctypes.c_int
+    L.gs_destroy.restype = None
+    L.gs_last_error.restype = ctypes.c_char_p
+    L.gs_launch_count.restype = c_int64
+    if path is None:
+        _lib = L
+    return L
+
+
+# ---------------------------------------------------------------- marshalling
+def camera_struct(cam) -> GsCamera:
+    c = GsCamera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.tan_fovx, c.tan_fovy = float(cam.tan_fovx), float(cam.tan_fovy)
+    c.near_z = float(getattr(cam, "near_z", 0.2))
+    vm = [float(x) for x in cam.viewmat.reshape(-1)]
+    c.viewmat[:] = vm
+    c.campos[:] = [float(x) for x in cam.campos.reshape(-1)]
+    return c
+
+
+def scene_struct(scene) -> GsScene:
+    for k in ("means", "scales", "rotations", "opacities", "sh"):
+        t = getattr(scene, k)
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError(f"scene.{k} must be a contiguous float32 CUDA tensor")
+    s = GsScene()
+    s.n = int(scene.means.shape[1])
+    s.sh_degree = int(scene.sh_degree)
+    s.means, s.scales = scene.means.data_ptr(), scene.scales.data_ptr()
+    s.rotations, s.opacities, s.sh = scene.rotations.data_ptr(), scene.opacities.data_ptr(), scene.sh.data_ptr()
+    return s
+
+
+def cfg_struct(tile: int, mode, bg=(0.0, 0.0, 0.0)) -> GsRasterCfg:
+    c = GsRasterCfg()
+    c.tile = int(tile)
+    c.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+    c.bg[:] = [float(x) for x in bg]
+    return c
+
+
+def frame_sizes(n: int, width: int, height: int, tile: int, key_capacity: int) -> GsFrameBytes:
+    out = GsFrameBytes()
+    st = load().gs_frame_sizes(int(n), int(width), int(height), int(tile), int(key_capacity), ctypes.byref(out))
+    if st != 0:
+        raise GsError(st, f"gs_frame_sizes(n={n}, {width}x{height}, tile={tile}, keys={key_capacity})")
+    return out
+
+
+class Frame:
+    """Caller-owned device buffers of one raster (gs_frame), allocated by torch."""
+
+    def __init__(self, n: int, width: int, height: int, tile: int, key_capacity: int, device=None):
+        device = torch.device(device or "cuda")
+        sz = frame_sizes(n, width, height, tile, key_capacity)
+        self.n, self.width, self.height, self.tile, self.key_capacity = n, width, height, tile, key_capacity
+        self.gx, self.gy = (width + tile - 1) // tile, (height + tile - 1) // tile
+        e = lambda nbytes, dt, es: torch.empty(max(nbytes // es, 1), dtype=dt, device=device)
+        self.proj = e(sz.proj, torch.float32, 4)
+        self.counts = e(sz.counts, torch.int32, 4)
+        self.keys = e(sz.keys, torch.int64, 8)
+        self.vals = e(sz.vals, torch.int32, 4)
+        self.ranges = e(sz.ranges, torch.int32, 4)
+        self.image = torch.empty(3, height, width, dtype=torch.float32, device=device)
+        self.final_T = torch.empty(height, width, dtype=torch.float32, device=device)
+        self.last = torch.empty(height, width, dtype=torch.int32, device=device)
+        self.scratch = e(sz.scratch, torch.uint8, 1)
+        self.bytes = sz
+        f = GsFrame()
+        f.n_capacity, f.key_capacity = n, key_capacity
+        f.width, f.height, f.tile = width, height, tile
+        f.proj, f.counts, f.keys, f.vals = (self.proj.data_ptr(), self.counts.data_ptr(), self.keys.data_ptr(),
+                                            self.vals.data_ptr())
+        f.ranges, f.image, f.final_T, f.last = (self.ranges.data_ptr(), self.image.data_ptr(),
+                                                self.final_T.data_ptr(), self.last.data_ptr())
+        f.scratch = self.scratch.data_ptr()
+        self.struct = f
+
+    # views (valid after the corresponding stage has run)
+    def proj_planes(self):
+        return self.proj[: 3 * self.n * 4].view(3, self.n, 4)
+
+    def sorted_pairs(self, K: int):
+        return self.keys[:K], self.vals[:K]
+
+    def unsorted_pairs(self, K: int):
+        return self.keys[:K], self.vals[:K]
+
+    def tile_ranges(self):
+        return self.ranges[: self.gx * self.gy * 2].view(self.gx * self.gy, 2)
+
+    def nbytes(self) -> int:
+        s = self.bytes
+        return s.proj + s.counts + s.keys + s.vals + s.ranges + s.image + s.final_T + s.last + s.scratch
+
+
+class Rasterizer:
+    """A gs_context bound to one device and stream, with the six stage calls."""
+
+    def __init__(self, device=None, stream=None):
+        self.lib = load()
+        self.device = torch.device(device or "cuda")
+        idx = self.device.index if self.device.index is not None else torch.cuda.current_device()
+        self.device = torch.device("cuda", idx)
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        ctx = c_void_p()
+        st = self.lib.gs_create(idx, c_void_p(s.cuda_stream), ctypes.byref(ctx))
+        if st != 0:
+            raise GsError(st, "gs_create failed")
+        self.ctx = ctx
+        self.stream = s
+
+    def __del__(self):
+        ctx = getattr(self, "ctx", None)
+        if ctx and getattr(self, "lib", None) is not None:
+            self.lib.gs_destroy(ctx)
+            self.ctx = None
+
+    def set_stream(self, stream):
+        self.stream = stream
+        self._check(self.lib.gs_set_stream(self.ctx, c_void_p(stream.cuda_stream)), "gs_set_stream")
+
+    def _check(self, st: int, what: str):
+        if st != 0:
+            raise GsError(st, f"{what}: {self.lib.gs_last_error(self.ctx).decode(errors='replace')}")
+
+    def launch_count(self) -> int:
+        return int(self.lib.gs_launch_count(self.ctx))
+
+    # ---- stages (names follow gs.h)
+    def gs_preprocess(self, scene, cam, cfg, frame: Frame):
+        s, c = scene_struct(scene), camera_struct(cam)
+        self._check(self.lib.gs_preprocess(self.ctx, ctypes.byref(s), ctypes.byref(c), ctypes.byref(cfg),
+                                           ctypes.byref(frame.struct)), "gs_preprocess")
+
+    def gs_intersect(self, cam, cfg, frame: Frame, sync: bool = False):
+        c = camera_struct(cam)
+        if sync:
+            k = c_int64(0)
+            st = self.lib.gs_intersect(self.ctx, ctypes.byref(c), ctypes.byref(cfg), ctypes.byref(frame.struct),
+                                       ctypes.byref(k))
+            if st == 3:
+                return int(k.value)
+            self._check(st, "gs_intersect")
+            return int(k.value)
+        self._check(self.lib.gs_intersect(self.ctx, ctypes.byref(c), ctypes.byref(cfg), ctypes.byref(frame.struct),
+                                          None), "gs_intersect")
+        return None
+
+    def gs_sort(self, cam, cfg, frame: Frame):
+        c = camera_struct(cam)
+        self._check(self.lib.gs_sort(self.ctx, ctypes.byref(c), ctypes.byref(cfg), ctypes.byref(frame.struct)),
+                    "gs_sort")
+
+    def gs_tile_ranges(self, cam, cfg, frame: Frame):
+        c = camera_struct(cam)
+        self._check(self.lib.gs_tile_ranges(self.ctx, ctypes.byref(c), ctypes.byref(cfg),
+                                             ctypes.byref(frame.struct)), "gs_tile_ranges")
+
+    def gs_render(self, cam, cfg, frame: Frame):
+        c = camera_struct(cam)
+        self._check(self.lib.gs_render(self.ctx, ctypes.byref(c), ctypes.byref(cfg), ctypes.byref(frame.struct)),
+                    "gs_render")
+
+    def gs_forward(self, scene, cam, cfg, frame: Frame):
+        s, c = scene_struct(scene), camera_struct(cam)
+        self._check(self.lib.gs_forward(self.ctx, ctypes.byref(s), ctypes.byref(c), ctypes.byref(cfg),
+                                        ctypes.byref(frame.struct)), "gs_forward")
+
+    def gs_read_status(self, frame: Frame, raise_on_error: bool = True):
+        k = c_int64(0)
+        fl = c_uint32(0)
+        st = self.lib.gs_read_status(self.ctx, ctypes.byref(frame.struct), ctypes.byref(k), ctypes.byref(fl))
+        if raise_on_error and st not in (0,):
+            self._check(st, "gs_read_status")
+        return int(k.value), int(fl.value)
+
+
+@dataclass
+class RenderOutput:
+    image: torch.Tensor
+    final_T: torch.Tensor
+    last: torch.Tensor
+    num_keys: int
+    frame: Frame
+
+
+class Renderer:
+    """Forward renderer that owns frames and grows the key capacity on demand.
+
+    ``render`` runs the five stages asynchronously, then reads the frame
+    status (one synchronisation); if the keys did not fit it grows the
+    capacity to ``headroom`` x K and re-runs intersect, sort, ranges and render.
+    """
+
+    def __init__(self, device=None, stream=None, headroom: float = 1.25):
+        self.rast = Rasterizer(device, stream)
+        self.headroom = headroom
+        self.frames = {}
+
+    def frame(self, n, width, height, tile, min_keys=0) -> Frame:
+        key = (n, width, height, tile)
+        f = self.frames.get(key)
+        if f is None or f.key_capacity < min_keys:
+            cap = min(MAX_KEYS, max(int(min_keys), 1 << 16, f.key_capacity if f else 0))
+            f = Frame(n, width, height, tile, cap, self.rast.device)
+            self.frames[key] = f
+        return f
+
+    def render(self, scene, cam, mode="accutile", tile: int = 16, bg=(0.0, 0.0, 0.0)) -> RenderOutput:
+        cfg = cfg_struct(tile, mode, bg)
+        n = int(scene.means.shape[1])
+        f = self.frame(n, cam.width, cam.height, tile)
+        r = self.rast
+        r.gs_preprocess(scene, cam, cfg, f)
+        r.gs_intersect(cam, cfg, f)
+        r.gs_sort(cam, cfg, f)
+        r.gs_tile_ranges(cam, cfg, f)
+        r.gs_render(cam, cfg, f)
+        K, flags = r.gs_read_status(f, raise_on_error=False)
+        if flags & FLAG_CAPACITY:
+            if K > MAX_KEYS:
+                raise GsError(3, f"{K} keys exceed the library maximum {MAX_KEYS}")
+            f = self.frame(n, cam.width, cam.height, tile, min_keys=int(K * self.headroom) + 1)
+            r.gs_preprocess(scene, cam, cfg, f)
+            r.gs_intersect(cam, cfg, f)
+            r.gs_sort(cam, cfg, f)
+            r.gs_tile_ranges(cam, cfg, f)
+            r.gs_render(cam, cfg, f)
+            K, flags = r.gs_read_status(f, raise_on_error=False)
+        if flags:
+            r.gs_read_status(f, raise_on_error=True)
+        return RenderOutput(f.image, f.final_T, f.last, K, f)

@@ -1,0 +1,258 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bar: integer work (tile counts, key totals, emitted pairs, sorted pairs,
+tile ranges, last-contributor indices) bit-exact against the FP32 oracle,
+which follows the same documented operation order; the per-Gaussian 2D state
+bit-exact; images within 1e-4 max abs error per channel (the FP64 oracle's
+error is printed beside it).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2412_00578_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+IMG_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def raster():
+    from paper_2412_00578_gb300 import build
+
+    build.build()
+    from paper_2412_00578_gb300 import raster as r
+
+    return r
+
+
+@pytest.fixture(scope="module")
+def rast(raster):
+    return raster.Rasterizer("cuda:0")
+
+
+def run_pipeline(raster, rast, scene, cam, mode, tile, bg=(0.0, 0.0, 0.0), n_capacity=None, key_capacity=None):
+    """Run the five stages through the C ABI, snapshotting each stage's output."""
+    dev_scene = scene.to("cuda:0")
+    n = scene.n
+    ncap = n if n_capacity is None else n_capacity
+    if key_capacity is None:
+        key_capacity = max(oracle.count_keys(scene, cam, tile, mode, prec64=False), 1)
+    frame = raster.Frame(ncap, cam.width, cam.height, tile, key_capacity, "cuda:0")
+    cfg = raster.cfg_struct(tile, mode, bg)
+    out = {}
+    rast.gs_preprocess(dev_scene, cam, cfg, frame)
+    torch.cuda.synchronize()
+    out["counts"] = frame.counts[:ncap].cpu().numpy()
+    out["proj"] = frame.proj_planes().cpu().numpy() if ncap > 0 else np.zeros((3, 0, 4), np.float32)
+    K = rast.gs_intersect(cam, cfg, frame, sync=True)
+    out["K"] = K
+    Ke = min(K, key_capacity)
+    out["keys_unsorted"] = frame.keys[:Ke].cpu().numpy().view(np.uint64).copy()
+    out["vals_unsorted"] = frame.vals[:Ke].cpu().numpy().view(np.uint32).copy()
+    rast.gs_sort(cam, cfg, frame)
+    rast.gs_tile_ranges(cam, cfg, frame)
+    rast.gs_render(cam, cfg, frame)
+    torch.cuda.synchronize()
+    out["keys"] = frame.keys[:Ke].cpu().numpy().view(np.uint64).copy()
+    out["vals"] = frame.vals[:Ke].cpu().numpy().view(np.uint32).copy()
+    out["ranges"] = frame.tile_ranges().cpu().numpy().view(np.uint32).copy()
+    out["image"] = frame.image.cpu().numpy()
+    out["final_T"] = frame.final_T.cpu().numpy()
+    out["last"] = frame.last.cpu().numpy().view(np.uint32)
+    out["frame"] = frame
+    return out
+
+
+def check_against_oracle(gpu, scene, cam, mode, tile, bg=(0.0, 0.0, 0.0), report_f64=False):
+    ref = oracle.render(scene, cam, tile, mode, bg=bg, prec64=False)
+    st, counts = oracle.preprocess(scene, cam, tile, mode, prec64=False)
+    n = scene.n
+    # counts and per-Gaussian 2D state
+    assert np.array_equal(gpu["counts"][:n], counts), "tile counts differ"
+    assert np.all(gpu["counts"][n:] == 0)
+    m = counts > 0
+    if m.any():
+        P = gpu["proj"][:, :n]
+        f32 = lambda a: a.astype(np.float32)
+        np.testing.assert_array_equal(P[0][m], f32(st[m][:, [0, 1, 3, 2]]))  # u v opacity depth
+        np.testing.assert_array_equal(P[1][m], f32(st[m][:, [4, 5, 6, 7]]))  # a b c t
+        np.testing.assert_array_equal(P[2][m][:, :3], f32(st[m][:, [8, 9, 10]]))  # rgb
+        assert np.array_equal(P[2][m][:, 3].view(np.int32), st[m][:, 14].astype(np.int32))  # radius
+    # key total and emitted pairs (compared per Gaussian, any order within one)
+    assert gpu["K"] == ref["num_keys"]
+    ku, vu = gpu["keys_unsorted"], gpu["vals_unsorted"]
+    o1 = np.lexsort((ku, vu))
+    o2 = np.lexsort((ref["keys_unsorted"], ref["vals_unsorted"]))
+    assert np.array_equal(vu[o1], ref["vals_unsorted"][o2]) and np.array_equal(ku[o1], ref["keys_unsorted"][o2])
+    # emission is grouped by Gaussian in index order
+    assert np.all(np.diff(vu.astype(np.int64)) >= 0)
+    # sort, ranges: bit-exact
+    assert np.array_equal(gpu["keys"], ref["keys"]), "sorted keys differ"
+    assert np.array_equal(gpu["vals"], ref["vals"]), "sorted values differ"
+    assert np.array_equal(gpu["ranges"], ref["ranges"]), "tile ranges differ"
+    # image
+    err = np.abs(gpu["image"].astype(np.float64) - ref["image"]).max() if gpu["image"].size else 0.0
+    assert err <= IMG_TOL, err
+    assert np.abs(gpu["final_T"].astype(np.float64) - ref["final_T"]).max() <= IMG_TOL
+    assert np.array_equal(gpu["last"], ref["last"])
+    if report_f64:
+        ref64 = oracle.render(scene, cam, tile, mode, bg=bg, prec64=True)
+        e64 = np.abs(gpu["image"].astype(np.float64) - ref64["image"]).max()
+        print(f"mode {mode} tile {tile}: K={gpu['K']} max|gpu-f32 oracle|={err:.3g} max|gpu-f64 oracle|={e64:.3g}")
+    return ref
+
+
+def ragged_case(n=3000, seed=31, w=97, h=61):
+    scene = synth.uniform_box_scene(n, seed=seed, log_scale_mu=-3.0)
+    cam = synth.pinhole(w, h, 60.0, np.eye(3), np.array([0.0, 0.0, 5.0]))
+    return scene, cam
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_ragged_small(raster, rast, mode, tile):
+    scene, cam = ragged_case()
+    gpu = run_pipeline(raster, rast, scene, cam, mode, tile, bg=(0.1, 0.2, 0.3))
+    check_against_oracle(gpu, scene, cam, mode, tile, bg=(0.1, 0.2, 0.3))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_box_16k_320x240(raster, rast, mode):
+    scene, cam = synth.small_box_workload()
+    gpu = run_pipeline(raster, rast, scene, cam, mode, 16)
+    check_against_oracle(gpu, scene, cam, mode, 16, report_f64=True)
+
+
+def test_orbit_camera_large_splats(raster, rast):
+    """Off-axis camera, bigger Gaussians (many tiles each, both sweep
+    directions, clipping at every image edge)."""
+    scene = synth.uniform_box_scene(4000, seed=32, half=3.0, log_scale_mu=-2.0, log_scale_sd=0.7)
+    cam = synth.look_at(211, 157, 60.0, (2.5, -1.5, -6.0), (0.3, 0.2, 0.1))
+    for mode in (0, 1, 2):
+        gpu = run_pipeline(raster, rast, scene, cam, mode, 16, bg=(0.5, 0.5, 0.5))
+        check_against_oracle(gpu, scene, cam, mode, 16, bg=(0.5, 0.5, 0.5))
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2])
+def test_sh_degrees(raster, rast, deg):
+    scene, cam = ragged_case(n=1500, seed=33)
+    scene.sh_degree = deg
+    gpu = run_pipeline(raster, rast, scene, cam, 2, 16)
+    check_against_oracle(gpu, scene, cam, 2, 16)
+
+
+def test_padding_capacity_beyond_n(raster, rast):
+    scene, cam = ragged_case(n=1000, seed=34)
+    gpu = run_pipeline(raster, rast, scene, cam, 2, 16, n_capacity=1000 + 4099)
+    check_against_oracle(gpu, scene, cam, 2, 16)
+
+
+def test_empty_scene_and_all_culled(raster, rast):
+    _, cam = ragged_case()
+    empty = synth.uniform_box_scene(0, seed=35)
+    gpu = run_pipeline(raster, rast, empty, cam, 2, 16, bg=(0.2, 0.3, 0.4), key_capacity=16)
+    assert gpu["K"] == 0
+    assert np.allclose(gpu["image"], np.array([0.2, 0.3, 0.4], np.float32)[:, None, None])
+    assert np.all(gpu["final_T"] == 1.0) and np.all(gpu["last"] == 0) and np.all(gpu["ranges"] == 0)
+    behind = synth.uniform_box_scene(2000, seed=36)
+    behind.means[2] -= 20.0  # all behind the camera
+    gpu = run_pipeline(raster, rast, behind, cam, 2, 16, key_capacity=16)
+    assert gpu["K"] == 0 and np.all(gpu["counts"] == 0)
+
+
+def test_screen_filling_gaussian(raster, rast):
+    """One large opaque Gaussian in front of the camera touches every tile."""
+    scene = synth.uniform_box_scene(1, seed=37)
+    scene.means[:] = torch.tensor([[0.0], [0.0], [-3.0]])
+    scene.scales[:] = 5.0
+    scene.opacities[:] = 0.99
+    cam = synth.pinhole(100, 75, 60.0, np.eye(3), np.array([0.0, 0.0, 5.0]))
+    for mode in (0, 1, 2):
+        gpu = run_pipeline(raster, rast, scene, cam, mode, 16)
+        assert gpu["K"] == 7 * 5
+        check_against_oracle(gpu, scene, cam, mode, 16)
+
+
+def test_capacity_overflow_reports_and_renderer_recovers(raster, rast):
+    scene, cam = ragged_case(n=2000, seed=38)
+    K = oracle.count_keys(scene, cam, 16, 2)
+    frame = raster.Frame(scene.n, cam.width, cam.height, 16, K - 1, "cuda:0")
+    cfg = raster.cfg_struct(16, 2)
+    rast.gs_preprocess(scene.to("cuda:0"), cam, cfg, frame)
+    assert rast.gs_intersect(cam, cfg, frame, sync=True) == K
+    Kr, flags = rast.gs_read_status(frame, raise_on_error=False)
+    assert Kr == K and flags & raster.FLAG_CAPACITY
+    with pytest.raises(raster.GsError) as ei:
+        rast.gs_read_status(frame)
+    assert ei.value.status == 3
+    r = raster.Renderer("cuda:0")
+    r.frames[(scene.n, cam.width, cam.height, 16)] = raster.Frame(scene.n, cam.width, cam.height, 16, 100, "cuda:0")
+    out = r.render(scene.to("cuda:0"), cam, "accutile", 16)
+    ref = oracle.render(scene, cam, 16, 2, prec64=False)
+    assert out.num_keys == K
+    assert np.abs(out.image.cpu().numpy() - ref["image"]).max() <= IMG_TOL
+
+
+def test_invalid_arguments_are_rejected(raster, rast):
+    scene, cam = ragged_case(n=10, seed=39)
+    frame = raster.Frame(10, cam.width, cam.height, 16, 64, "cuda:0")
+    ds = scene.to("cuda:0")
+    with pytest.raises(raster.GsError) as ei:
+        rast.gs_preprocess(ds, cam, raster.cfg_struct(8, 2), frame)  # tile mismatch
+    assert ei.value.status == 1
+    with pytest.raises(raster.GsError):
+        rast.gs_preprocess(ds, cam, raster.cfg_struct(16, 7), frame)  # bad mode
+    other = synth.pinhole(50, 50, 60.0, np.eye(3), np.zeros(3))
+    with pytest.raises(raster.GsError):
+        rast.gs_render(other, raster.cfg_struct(16, 2), frame)  # camera/frame size mismatch
+    big = synth.uniform_box_scene(11, seed=40).to("cuda:0")
+    with pytest.raises(raster.GsError):
+        rast.gs_preprocess(big, cam, raster.cfg_struct(16, 2), frame)  # n > n_capacity
+
+
+def test_repeatable_bit_for_bit(raster, rast):
+    scene, cam = synth.small_box_workload()
+    a = run_pipeline(raster, rast, scene, cam, 2, 16)
+    b = run_pipeline(raster, rast, scene, cam, 2, 16)
+    for k in ("keys", "vals", "ranges", "image", "last"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+# ---------------------------------------------------------------- full size
+@pytest.fixture(scope="module")
+def outdoor():
+    return synth.outdoor_workload()
+
+
+@pytest.mark.parametrize("mode", [2, 0])
+def test_outdoor_3m_1280x840_full_frame(raster, outdoor, mode):
+    """The 3M-Gaussian 1280x840 workload in the launch configuration the
+    benchmark times (gs_forward, tile 16): every key, range and pixel."""
+    scene, cam = outdoor
+    r = raster.Renderer("cuda:0")
+    out = r.render(scene.to("cuda:0"), cam, mode=mode, tile=16)
+    torch.cuda.synchronize()
+    ref = oracle.render(scene, cam, 16, mode, prec64=False)
+    K = out.num_keys
+    assert K == ref["num_keys"]
+    assert np.array_equal(out.frame.keys[:K].cpu().numpy().view(np.uint64), ref["keys"])
+    assert np.array_equal(out.frame.vals[:K].cpu().numpy().view(np.uint32), ref["vals"])
+    assert np.array_equal(out.frame.tile_ranges().cpu().numpy().view(np.uint32), ref["ranges"])
+    err = np.abs(out.image.cpu().numpy().astype(np.float64) - ref["image"]).max()
+    assert err <= IMG_TOL, err
+    print(f"outdoor 3M mode {mode}: K={K}, image max abs err {err:.3g}")
+
+
+def test_outdoor_pruned_300k(raster, outdoor):
+    scene, cam = outdoor
+    pruned = synth.prune_random(scene, 300_000, seed=1)
+    r = raster.Renderer("cuda:0")
+    out = r.render(pruned.to("cuda:0"), cam, mode="accutile", tile=16)
+    torch.cuda.synchronize()
+    ref = oracle.render(pruned, cam, 16, 2, prec64=False)
+    assert out.num_keys == ref["num_keys"]
+    assert np.array_equal(out.frame.keys[:out.num_keys].cpu().numpy().view(np.uint64), ref["keys"])
+    assert np.abs(out.image.cpu().numpy().astype(np.float64) - ref["image"]).max() <= IMG_TOL
