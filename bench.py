@@ -1,0 +1,427 @@
+"""Benchmark of the GB300 tile rasterizer (forward render, Speedy-Splat localization).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload: the 3M-Gaussian outdoor-like scene at 1280x840 (blob mixture plus
+background shell, seed 0), tile 16.  One step is one full forward frame:
+preprocess -> intersect (scan + emit) -> radix sort -> tile ranges -> blend.
+``value`` is AccuTile frames/s with the scene resident in HBM (CUDA events on
+the rendering stream, W warm-up frames, then exactly K timed frames bracketed
+by barrier + synchronize, max over ranks).  The scene (708 MB) is larger than
+L2 (129 MB), so no L2 flush is inserted between frames.  The 3-sigma and
+SnugBox modes of the same library are timed the same way for the comparison.
+
+Multi-GPU (torchrun, N ranks): every rank renders its own frames of a full
+replica of the scene (the path does not shard a frame); value = frames of all
+ranks / max elapsed.
+
+``--impl reference`` times the CPU oracle (single thread, FP32, the
+documented operation order) on the host cores on the same workload; each step
+renders one horizontal band of the frame through the whole oracle pipeline,
+so the run stays within minutes; value = 1 / (bands x mean band time).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ms/frame & FPS, AccuTile vs 3-sigma box on 1 GB300; served p50/p99 ms"
+WORKLOAD = "outdoor-3M-1280x840"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=3_000_000)
+    p.add_argument("--width", type=int, default=1280)
+    p.add_argument("--height", type=int, default=840)
+    p.add_argument("--tile", type=int, default=16)
+    p.add_argument("--modes", default="accutile,snugbox,3sigma",
+                   help="modes to time; the first is the headline (profiling runs pass one mode)")
+    p.add_argument("--stage-steps", type=int, default=10, help="frames per mode for the per-stage breakdown (0: skip)")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples SM clock / power / throttle reasons with nvidia-smi every 200 ms."""
+
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            rows.append(parts)
+        if self.bus_id:
+            mine = [r for r in rows if r[1].lower().endswith(self.bus_id[-12:])]
+            rows = mine or rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        idx = rows[0][0]
+        rows = [r for r in rows if r[0] == idx]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        smax = max((num(r[3]) or 0.0) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[6 + k].lower().startswith("active")})
+        loaded = [s for s in sm if s >= 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max((num(r[4]) or 0.0) for r in rows)}
+
+
+# ---------------------------------------------------------------- helpers
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "src": "measured", "sm_max_mhz": float(d.get("sm_max_mhz", 2070))}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "src": "fallback", "sm_max_mhz": 2070.0}
+
+
+def workload(args):
+    from paper_2412_00578_gb300 import synth
+
+    scene, cam = synth.outdoor_workload(n=args.n, width=args.width, height=args.height)
+    return scene, cam
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2412_00578_gb300 import synth
+
+    oracle.build()
+    scene, cam = workload(args)
+    H = cam.height
+
+    def band_cam(y0, h):
+        c = synth.Camera(cam.width, h, cam.fx, cam.fy, cam.cx, cam.cy - y0, cam.tan_fovx, cam.tan_fovy,
+                         cam.viewmat, cam.campos, cam.near_z)
+        return c
+
+    # first warm-up step: one full frame, which also sizes the band count so the
+    # whole run stays within about 150 s
+    t0 = time.perf_counter()
+    oracle.render(scene, cam, args.tile, 2, prec64=False)
+    t_full = time.perf_counter() - t0
+    remaining = max(args.steps + args.warmup - 1, 1)
+    bands = max(1, min(16, math.ceil(remaining * t_full / 150.0)))
+    bh = math.ceil(H / bands)
+    times = []
+    for s in range(args.warmup - 1 + args.steps):
+        b = s % bands
+        y0 = b * bh
+        c = band_cam(y0, min(bh, H - y0))
+        t0 = time.perf_counter()
+        oracle.render(scene, c, args.tile, 2, prec64=False)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup - 1:
+            times.append(dt)
+    mean_band = sum(times) / len(times)
+    fps = 1.0 / (bands * mean_band)
+    sample = (f"CPU oracle (FP32, single thread), AccuTile, {args.n} Gaussians; each step renders one of {bands} "
+              f"horizontal bands ({cam.width}x{bh}) of the {cam.width}x{H} frame through the whole pipeline "
+              f"(every Gaussian preprocessed per band); first full frame took {t_full:.2f} s")
+    emit({"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
+          "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_band * 1e3,
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+          "config": {"workload": WORKLOAD, "gaussians": args.n, "width": cam.width, "height": H, "tile": args.tile,
+                     "mode": "accutile", "l2": "inputs exceed L2"},
+          "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": sample},
+          "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2412_00578_gb300 import build, raster
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    scene_cpu, cam = workload(args)
+    scene = scene_cpu.to(dev)
+    renderer = raster.Renderer(dev)
+    rast = renderer.rast
+    stream = rast.stream
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    modes = [m for m in args.modes.split(",") if m]
+    assert modes and modes[0] == "accutile", "the headline mode is accutile"
+    frames = {}
+    keys = {}
+    for m in modes:  # size each mode's frame (one synchronising render)
+        out = renderer.render(scene, cam, m, args.tile)
+        keys[m] = out.num_keys
+        frames[m] = out.frame
+
+    def timed(mode, steps, warmup, sampler=None):
+        cfg = raster.cfg_struct(args.tile, mode)
+        f = frames[mode]
+        for _ in range(warmup):
+            rast.gs_forward(scene, cam, cfg, f)
+        barrier()
+        if sampler:
+            sampler.start()
+        l0 = rast.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            rast.gs_forward(scene, cam, cfg, f)
+        e1.record(stream)
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        launches = rast.launch_count() - l0
+        ms = max_over_ranks(e0.elapsed_time(e1)) / steps
+        K, flags = rast.gs_read_status(f, raise_on_error=False)
+        if flags:
+            raise RuntimeError(f"device status flags {flags} after timed loop ({mode})")
+        return ms, launches, clocks
+
+    def stage_breakdown(mode, steps):
+        cfg = raster.cfg_struct(args.tile, mode)
+        f = frames[mode]
+        names = ["preprocess", "intersect", "sort", "tile_ranges", "render"]
+        acc = [0.0] * 5
+        for _ in range(steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+            ev[0].record(stream)
+            rast.gs_preprocess(scene, cam, cfg, f)
+            ev[1].record(stream)
+            rast.gs_intersect(cam, cfg, f)
+            ev[2].record(stream)
+            rast.gs_sort(cam, cfg, f)
+            ev[3].record(stream)
+            rast.gs_tile_ranges(cam, cfg, f)
+            ev[4].record(stream)
+            rast.gs_render(cam, cfg, f)
+            ev[5].record(stream)
+            torch.cuda.synchronize(dev)
+            for k in range(5):
+                acc[k] += ev[k].elapsed_time(ev[k + 1])
+        return {n: a / steps for n, a in zip(names, acc)}
+
+    bus = None
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        bus = f"{props.pci_bus_id:02x}:{props.pci_device_id:02x}" if hasattr(props, "pci_bus_id") else None
+    except Exception:
+        bus = None
+
+    # --- headline: AccuTile, K timed frames
+    sampler = ClockSampler(None)
+    ms_acc, launches, clocks = timed("accutile", args.steps, args.warmup, sampler)
+    per_mode = {"accutile": {"ms_per_frame": ms_acc, "fps": 1e3 / ms_acc, "keys": keys["accutile"]}}
+    for m in modes[1:]:
+        ms, _, _ = timed(m, max(10, args.steps // 2), args.warmup)
+        per_mode[m] = {"ms_per_frame": ms, "fps": 1e3 / ms, "keys": keys[m]}
+    stages = {m: stage_breakdown(m, max(args.stage_steps, 1)) for m in modes} if args.stage_steps > 0 else {}
+
+    # --- roofline of the dominant kernel (from the AccuTile stage breakdown)
+    pk = peaks()
+    cfg_acc = raster.cfg_struct(args.tile, "accutile")
+    f_acc = frames["accutile"]
+    rast.gs_forward(scene, cam, cfg_acc, f_acc)
+    ev_pairs, contrib_pairs, exec_pairs = rast.gs_render_stats(cam, cfg_acc, f_acc)
+    counts = f_acc.counts[: scene.n]
+    n_counted = int((counts > 0).sum().item())
+    n = scene.n
+    K = keys["accutile"]
+    hw = cam.width * cam.height
+    sh_bytes = 4 * 3 * (scene.sh_degree + 1) ** 2
+    st = stages["accutile"] if stages else stage_breakdown("accutile", 1)
+    stage_bytes = {
+        # geometry + opacity for all, SH + 48 B state for counted, 4 B count each
+        "preprocess": n * (40 + 4) + n_counted * (sh_bytes + 48),
+        # counts read twice, 2D state read once per counted Gaussian, 12 B per key written
+        "intersect": n * 8 + n_counted * 48 + K * 12,
+        # one histogram read (8 B/key) + per pass read and write of key and value (24 B/key)
+        "sort": K * 8 + K * 24 * raster_sort_passes(cam.width, cam.height, args.tile),
+        "tile_ranges": K * 8 + (cam.width // args.tile + 1) * (cam.height // args.tile + 1) * 8,
+        "render": K * (4 + 48) + hw * 20,
+    }
+    stage_frac = {k: {"ms": st[k], "gbs": stage_bytes[k] / (st[k] * 1e-3) / 1e9,
+                      "hbm_frac": stage_bytes[k] / (st[k] * 1e-3) / 1e9 / pk["hbm_gbs"]} for k in st}
+    # blend algorithmic work: 10 FP32 flops per evaluated pair (dx, dy, 2b dy, c dy dy,
+    # two fma, compare), 30 more per contributing pair (exp(-q/2) polynomial of 8 fma +
+    # reduction, alpha, T (1 - alpha), stop test, alpha T, 3 fma).
+    blend_flops = 10 * ev_pairs + 30 * contrib_pairs
+    sm_mhz = (clocks or {}).get("sm_mhz") or pk["sm_max_mhz"]
+    fp32_peak_tflops = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    dominant = max(st, key=st.get)
+    if dominant == "render":
+        achieved = blend_flops / (st["render"] * 1e-3) / 1e12
+        roof = {"kernel": "blend_kernel<16>", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "work": {"evaluated_pairs": ev_pairs, "contributing_pairs": contrib_pairs, "flops": blend_flops,
+                         "executed_pairs_after_culling": exec_pairs},
+                "peak_src": f"152 SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz"}
+    else:
+        achieved = stage_bytes[dominant] / (st[dominant] * 1e-3) / 1e9
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_src": pk["src"]}
+
+    # --- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = {k: getattr(scene_cpu, k).pin_memory() for k in ("means", "scales", "rotations", "opacities", "sh")}
+        img_host = torch.empty(3, cam.height, cam.width, dtype=torch.float32).pin_memory()
+        h2d = sum(v.numel() * 4 for v in host.values())
+        d2h = img_host.numel() * 4
+        e2e_steps = min(args.steps, 20)
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                for k, v in host.items():
+                    getattr(scene, k).copy_(v, non_blocking=True)
+            rast.gs_forward(scene, cam, cfg_acc, f_acc)
+            with torch.cuda.stream(stream):
+                img_host.copy_(f_acc.image, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(e2e_steps):
+            e2e_step()
+        a1.record(stream)
+        barrier()
+        ms_e2e = max_over_ranks(a0.elapsed_time(a1)) / e2e_steps
+        e2e = {"value": world * 1e3 / ms_e2e, "unit": "frames/s", "ms_per_frame": ms_e2e,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "path": "pinned host scene -> device copy, gs_forward, image -> pinned host, per frame"}
+
+    # --- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        t0 = time.perf_counter()
+        ref = oracle.render(scene_cpu, cam, args.tile, 2, prec64=False)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
+               "sample": f"one full {cam.width}x{cam.height} AccuTile frame of the {n}-Gaussian scene, FP32 oracle, "
+                         f"single thread ({dt:.1f} s)"}
+        img = f_acc.image.cpu().numpy()
+        cpu["image_max_abs_err_vs_gpu"] = float(abs(img.astype("float64") - ref["image"]).max())
+
+    if rank == 0:
+        fps = world * 1e3 / ms_acc
+        emit({"metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms_acc, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+              "config": {"workload": WORKLOAD, "gaussians": n, "width": cam.width, "height": cam.height,
+                         "tile": args.tile, "mode": "accutile", "l2": "inputs exceed L2 (708 MB scene), no flush",
+                         "parallelism": f"replicas x{world}"},
+              "ms_per_frame": ms_acc, "modes": per_mode,
+              "speedup_vs_3sigma": (per_mode["3sigma"]["ms_per_frame"] / ms_acc) if "3sigma" in per_mode else None,
+              "stages_ms": stages, "stage_roofline": stage_frac,
+              "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+              "cpu_baseline": cpu})
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def raster_sort_passes(width, height, tile):
+    tiles = ((width + tile - 1) // tile) * ((height + tile - 1) // tile)
+    b = 0
+    while (1 << b) < tiles:
+        b += 1
+    bits = 32 + b
+    return 2 * ((bits + 15) // 16)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -184,9 +184,51 @@ gs_status gs_tile_ranges(gs_context* ctx, const gs_camera* cam, const gs_raster_
  * add T * bg.  Writes image, final_T and last. */
 gs_status gs_render(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame);
 
+/* Instrumented render: the same blend as gs_render (same outputs), which
+ * also counts, over all pixels: *evaluated = the (pixel, Gaussian) pairs the
+ * tile-list definition evaluates (each entry of the pixel's tile list up to
+ * and including the one that stops the pixel), *contributed = the pairs that
+ * add to the colour, *executed = the pairs whose q the kernel actually
+ * computed after its in-tile culling.  Synchronises the stream; host
+ * outputs, nullable.  States the blend's algorithmic work; not for timing. */
+gs_status gs_render_stats(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame,
+                          uint64_t* evaluated, uint64_t* contributed, uint64_t* executed);
+
 /* The five stages above in one call, with no host synchronisation. */
 gs_status gs_forward(gs_context* ctx, const gs_scene* scene, const gs_camera* cam, const gs_raster_cfg* cfg,
                      const gs_frame* frame);
+
+/* Gradients of the render (device, caller-owned), planar like gs_scene:
+ *   means [3][n], scales [3][n], rotations [4][n], opacities [n], sh [16][3][n]
+ *   (overwritten), means2d [2][n] (nullable, overwritten): dL/d(u, v), the
+ *   view-space gradient used by densification heuristics,
+ *   score [n] (nullable): the efficient pruning score of Sec. 4.2.1,
+ *   sum over pixels and channels of (dC/dg_i)^2, is ADDED to it so views can
+ *   be accumulated,
+ *   work: library scratch of gs_backward_work_bytes(n_capacity) bytes. */
+typedef struct gs_grads {
+    float* means;
+    float* scales;
+    float* rotations;
+    float* opacities;
+    float* sh;
+    float* means2d;
+    float* score;
+    float* work;
+} gs_grads;
+
+/* Bytes of gs_grads.work for a frame of n_capacity Gaussians. */
+int64_t gs_backward_work_bytes(int64_t n_capacity);
+
+/* Render backward (Sec. 4.2, 4.2.1): given dL/dimage ([3][height][width],
+ * device) for the image the frame holds (a completed gs_forward of this
+ * scene, camera and cfg), write dL/d(means, scales, rotations, opacities,
+ * sh), optionally dL/d(u, v), and add the pruning score.  Per pixel, the
+ * tile list is walked back to front from its last contributor; threshold,
+ * 0.99 clamp and stop decisions are those of the forward.  Accumulation uses
+ * atomics, so results are reproducible to rounding, not bit for bit. */
+gs_status gs_render_backward(gs_context* ctx, const gs_scene* scene, const gs_camera* cam, const gs_raster_cfg* cfg,
+                             const gs_frame* frame, const float* dL_dimage, const gs_grads* grads);
 
 /* Synchronise the stream and read the frame's device status: the key total
  * K and the GS_FLAG_* bits (both host outputs, nullable).  Returns

@@ -73,6 +73,8 @@ def _declare(L):
     L.oracle_render.restype = I32
     L.oracle_render_notile.argtypes = [I32, I64, P, P, P, P, P, I32, I32, I32, P, P, P, P, I32, P]
     L.oracle_blend_pixel.argtypes = [I32, P, I64, ctypes.c_double, ctypes.c_double, P, P]
+    L.oracle_backward.argtypes = [I64, P, P, P, P, P, I32, I32, I32, P, I32, I32, P, P, P, P]
+    L.oracle_sh_basis_grad.argtypes = [P, P, I64]
 
 
 def _ptr(a: np.ndarray):
@@ -220,3 +222,33 @@ def blend_pixel(gaussians, px: float, py: float, bg=(0.0, 0.0, 0.0), prec64: boo
     out = np.zeros(5, np.float64)
     lib().oracle_blend_pixel(int(prec64), _ptr(g), g.shape[0], float(px), float(py), _ptr(bgv), _ptr(out))
     return out[:3].copy(), float(out[3]), int(out[4])
+
+
+# ------------------------------------------------------------------ backward
+GRAD_SLICES = {"means": (0, 3), "scales": (3, 6), "rotations": (6, 10), "opacities": (10, 11), "sh": (11, 59)}
+G2D_FIELDS = ["u", "v", "a", "b", "c", "sigma", "r", "g", "b_", "score"]
+
+
+def backward(scene, cam, dL_dimage, tile: int = 16, mode: int = 2, bg=(0.0, 0.0, 0.0)):
+    """FP64 gradients of L = sum(dL_dimage * image) for one tile mode.
+    Returns (grads, g2d): grads maps each scene array name to an array shaped
+    like it; g2d is [10, n] (du dv da db dc dsigma dr dg db score)."""
+    n, (m, s, r, o, sh), deg = _scene_arrays(scene)
+    w, h, cf = _cam(cam)
+    G = np.ascontiguousarray(np.asarray(dL_dimage, np.float64).reshape(3, h, w))
+    bgv = np.asarray(bg, np.float32)
+    grads = np.zeros((59, n), np.float64)
+    g2d = np.zeros((10, n), np.float64)
+    lib().oracle_backward(n, _ptr(m), _ptr(s), _ptr(r), _ptr(o), _ptr(sh), deg, w, h, _ptr(cf), tile, mode, _ptr(bgv),
+                          _ptr(G), _ptr(grads), _ptr(g2d))
+    out = {k: grads[a:b] for k, (a, b) in GRAD_SLICES.items()}
+    out["sh"] = out["sh"].reshape(16, 3, n)
+    out["opacities"] = out["opacities"].reshape(n)
+    return out, g2d
+
+
+def sh_basis_grad(dirs) -> np.ndarray:
+    d = _np(dirs, np.float64).reshape(-1, 3)
+    out = np.empty((d.shape[0], 16, 3), np.float64)
+    lib().oracle_sh_basis_grad(_ptr(d), _ptr(out), d.shape[0])
+    return out

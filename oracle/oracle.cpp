@@ -678,6 +678,236 @@ void render_notile_impl(const SceneIn& s, int width, int height, const float* ca
     if (decisions_differ) *decisions_differ = differ;
 }
 
+// ---------------------------------------------------------------- backward
+// Gradients of L = sum_p sum_ch dL/dC_ch(p) C_ch(p) with respect to every
+// Gaussian parameter (Sec. 4.2: the render backward aggregates per-pixel
+// gradients into the 2D parameters, then a per-Gaussian pass carries them to
+// mu, s, r, h, sigma).  Also the efficient pruning score (Sec. 4.2.1):
+// score_i = sum_p sum_ch (dC_ch(p) / dg_i(p))^2, with dC/dg = sigma dC/dalpha
+// where alpha = sigma g is not clamped at 0.99, else 0.  Threshold, stop and
+// clamp decisions are held fixed (they are piecewise constant).
+//
+// Blend part, per pixel: with contributors i in front-to-back order,
+// transmittance T_i before i and T_f after the last,
+//   dC/dc_i = alpha_i T_i,
+//   dC/dalpha_i = T_i (c_i - B_i),  B_last = bg,  B_{i-1} = alpha_i c_i + (1 - alpha_i) B_i,
+// (B_i is the colour behind i seen through i's hole), then
+//   dalpha/dsigma = g, dalpha/dg = sigma, dg/dq = -g/2,
+//   q = a dx^2 + 2 b dx dy + c dy^2, dx = px - u, dy = py - v.
+struct Grad2D {
+    double u = 0, v = 0, a = 0, b = 0, c = 0, sigma = 0, rgb[3] = {0, 0, 0}, score = 0;
+};
+
+template <typename R> struct Contrib {
+    uint32_t idx;
+    R alpha, g, T, q, dx, dy;
+    bool clamped;
+};
+
+void blend_backward_pixel(const std::vector<Proj<double>>& P, const uint32_t* list, uint32_t len, double pxf,
+                          double pyf, const double* G, const float* bg, std::vector<Grad2D>& acc) {
+    // forward replay (records each contributor's alpha and T)
+    std::vector<Contrib<double>> cs;
+    double T = 1.0;
+    for (uint32_t k = 0; k < len; ++k) {
+        const Proj<double>& g = P[list[k]];
+        double dx = pxf - g.u, dy = pyf - g.v;
+        double q = std::fma(dx, std::fma(g.a, dx, (g.b + g.b) * dy), (g.c * dy) * dy);
+        if (!(q <= g.t)) continue;
+        double gg = std::exp(-0.5 * q);
+        double raw = g.opacity * gg;
+        double alpha = std::min(0.99, raw);
+        double Tn = T * (1.0 - alpha);
+        if (Tn < 1e-4) break;
+        cs.push_back({list[k], alpha, gg, T, q, dx, dy, raw > 0.99});
+        T = Tn;
+    }
+    double B[3] = {bg[0], bg[1], bg[2]};
+    for (size_t m = cs.size(); m-- > 0;) {
+        const Contrib<double>& e = cs[m];
+        const Proj<double>& g = P[e.idx];
+        Grad2D& A = acc[e.idx];
+        double dC_dalpha[3], dL_dalpha = 0.0;
+        for (int ch = 0; ch < 3; ++ch) {
+            dC_dalpha[ch] = e.T * (g.rgb[ch] - B[ch]);
+            dL_dalpha += G[ch] * dC_dalpha[ch];
+            A.rgb[ch] += G[ch] * e.alpha * e.T;
+        }
+        if (!e.clamped) {
+            A.sigma += dL_dalpha * e.g;
+            double dL_dq = dL_dalpha * g.opacity * (-0.5 * e.g);
+            A.a += dL_dq * e.dx * e.dx;
+            A.b += dL_dq * 2.0 * e.dx * e.dy;
+            A.c += dL_dq * e.dy * e.dy;
+            A.u += dL_dq * (-2.0 * g.a * e.dx - 2.0 * g.b * e.dy);
+            A.v += dL_dq * (-2.0 * g.b * e.dx - 2.0 * g.c * e.dy);
+            for (int ch = 0; ch < 3; ++ch) {
+                double dCdg = g.opacity * dC_dalpha[ch];
+                A.score += dCdg * dCdg;
+            }
+        }
+        for (int ch = 0; ch < 3; ++ch) B[ch] = e.alpha * g.rgb[ch] + (1.0 - e.alpha) * B[ch];
+    }
+}
+
+// Derivatives of the SH basis (in the order of sh_basis) with respect to
+// the unit direction (x, y, z): dY[k][0..2].
+void sh_basis_grad(double x, double y, double z, double dY[16][3]) {
+    const double C1 = kSh.c1, A2 = kSh.c2[0], C2 = kSh.c2[2], E2 = kSh.c2[4];
+    const double A3 = -kSh.c3[0], B3 = kSh.c3[1], C3 = -kSh.c3[2], D3 = kSh.c3[3], F3 = kSh.c3[5];
+    const double xx = x * x, yy = y * y, zz = z * z;
+    double g[16][3] = {
+        {0, 0, 0},
+        {0, -C1, 0},
+        {0, 0, C1},
+        {-C1, 0, 0},
+        {A2 * y, A2 * x, 0},
+        {0, -A2 * z, -A2 * y},
+        {-2 * C2 * x, -2 * C2 * y, 4 * C2 * z},
+        {-A2 * z, 0, -A2 * x},
+        {2 * E2 * x, -2 * E2 * y, 0},
+        {-6 * A3 * x * y, -A3 * (3 * xx - 3 * yy), 0},
+        {B3 * y * z, B3 * x * z, B3 * x * y},
+        {2 * C3 * x * y, -C3 * (4 * zz - xx - 3 * yy), -8 * C3 * y * z},
+        {-6 * D3 * x * z, -6 * D3 * y * z, D3 * (6 * zz - 3 * xx - 3 * yy)},
+        {-C3 * (4 * zz - 3 * xx - yy), 2 * C3 * x * y, -8 * C3 * x * z},
+        {2 * F3 * x * z, -2 * F3 * y * z, F3 * (xx - yy)},
+        {-A3 * (3 * xx - 3 * yy), 6 * A3 * x * y, 0},
+    };
+    for (int k = 0; k < 16; ++k)
+        for (int j = 0; j < 3; ++j) dY[k][j] = g[k][j];
+}
+
+// Per-Gaussian chain from the 2D gradients to mu, s, q, h, sigma (FP64).
+// out: [59] = dmu[3] ds[3] dq[4] dsigma dh[16][3] (h as sh[k][ch]).
+void preprocess_backward_one(const SceneIn& s, int64_t i, const Cam<double>& cam, const Grad2D& gr, double* out) {
+    for (int k = 0; k < 59; ++k) out[k] = 0.0;
+    const int64_t n = s.n;
+    double mu[3] = {s.means[i], s.means[n + i], s.means[2 * n + i]};
+    double sc[3] = {s.scales[i], s.scales[n + i], s.scales[2 * n + i]};
+    double q[4] = {s.rots[i], s.rots[n + i], s.rots[2 * n + i], s.rots[3 * n + i]};
+    double p[3];
+    for (int r = 0; r < 3; ++r)
+        p[r] = cam.V[r][0] * mu[0] + cam.V[r][1] * mu[1] + cam.V[r][2] * mu[2] + cam.V[r][3];
+    const double x = p[0], y = p[1], z = p[2];
+    double nq = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    double qw = q[0] / nq, qx = q[1] / nq, qy = q[2] / nq, qz = q[3] / nq;
+    double Rm[3][3] = {{1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+                       {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
+                       {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
+    double M[3][3], S3[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) M[r][k] = Rm[r][k] * sc[k];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) S3[r][c] = M[r][0] * M[c][0] + M[r][1] * M[c][1] + M[r][2] * M[c][2];
+    const double limx = 1.3 * cam.tan_fovx, limy = 1.3 * cam.tan_fovy;
+    const double xz = x / z, yz = y / z;
+    const bool clx = xz < -limx || xz > limx, cly = yz < -limy || yz > limy;
+    const double tx = std::min(limx, std::max(-limx, xz)) * z, ty = std::min(limy, std::max(-limy, yz)) * z;
+    const double fx = cam.fx, fy = cam.fy;
+    double J[2][3] = {{fx / z, 0, -fx * tx / (z * z)}, {0, fy / z, -fy * ty / (z * z)}};
+    double T[2][3];
+    for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < 3; ++k) T[r][k] = J[r][0] * cam.V[0][k] + J[r][1] * cam.V[1][k] + J[r][2] * cam.V[2][k];
+    double TS[2][3];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c) TS[r][c] = T[r][0] * S3[0][c] + T[r][1] * S3[1][c] + T[r][2] * S3[2][c];
+    const double sxx = TS[0][0] * T[0][0] + TS[0][1] * T[0][1] + TS[0][2] * T[0][2] + 0.3;
+    const double sxy = TS[0][0] * T[1][0] + TS[0][1] * T[1][1] + TS[0][2] * T[1][2];
+    const double syy = TS[1][0] * T[1][0] + TS[1][1] * T[1][1] + TS[1][2] * T[1][2] + 0.3;
+    const double det = sxx * syy - sxy * sxy, d2 = det * det;
+    // conic (a, b, c) -> Sigma2D (sxx, sxy, syy); sxy is one variable
+    const double g_sxx = gr.a * (-syy * syy / d2) + gr.b * (sxy * syy / d2) + gr.c * (1.0 / det - sxx * syy / d2);
+    const double g_syy = gr.a * (1.0 / det - sxx * syy / d2) + gr.b * (sxy * sxx / d2) + gr.c * (-sxx * sxx / d2);
+    const double g_sxy = gr.a * (2.0 * sxy * syy / d2) + gr.b * (-1.0 / det - 2.0 * sxy * sxy / d2) +
+                         gr.c * (2.0 * sxy * sxx / d2);
+    // Sigma2D = T Sigma3D T^T: with G2 = [[g_sxx, g_sxy/2], [g_sxy/2, g_syy]],
+    // dL/dSigma3D = T^T G2 T, dL/dT = 2 G2 T Sigma3D
+    const double G2[2][2] = {{g_sxx, 0.5 * g_sxy}, {0.5 * g_sxy, g_syy}};
+    double G3[3][3], dT[2][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double acc = 0;
+            for (int m = 0; m < 2; ++m)
+                for (int k = 0; k < 2; ++k) acc += T[m][r] * G2[m][k] * T[k][c];
+            G3[r][c] = acc;
+        }
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 3; ++c) dT[r][c] = 2.0 * (G2[r][0] * TS[0][c] + G2[r][1] * TS[1][c]);
+    // T = J W -> dL/dJ = dL/dT W^T
+    double dJ[2][3];
+    for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < 3; ++k) dJ[r][k] = dT[r][0] * cam.V[k][0] + dT[r][1] * cam.V[k][1] + dT[r][2] * cam.V[k][2];
+    // J entries as functions of the camera-space mean (with the clamp)
+    double dp[3] = {0, 0, 0};
+    dp[2] += dJ[0][0] * (-fx / (z * z)) + dJ[1][1] * (-fy / (z * z));
+    if (!clx) {
+        dp[0] += dJ[0][2] * (-fx / (z * z));
+        dp[2] += dJ[0][2] * (2.0 * fx * x / (z * z * z));
+    } else {
+        dp[2] += dJ[0][2] * (fx * (tx / z) / (z * z));
+    }
+    if (!cly) {
+        dp[1] += dJ[1][2] * (-fy / (z * z));
+        dp[2] += dJ[1][2] * (2.0 * fy * y / (z * z * z));
+    } else {
+        dp[2] += dJ[1][2] * (fy * (ty / z) / (z * z));
+    }
+    // projected mean
+    dp[0] += gr.u * fx / z;
+    dp[1] += gr.v * fy / z;
+    dp[2] += gr.u * (-fx * x / (z * z)) + gr.v * (-fy * y / (z * z));
+    double dmu[3];
+    for (int k = 0; k < 3; ++k) dmu[k] = cam.V[0][k] * dp[0] + cam.V[1][k] * dp[1] + cam.V[2][k] * dp[2];
+    // Sigma3D = M M^T -> dL/dM = 2 G3 M; M = R S
+    double dM[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < 3; ++k) dM[r][k] = 2.0 * (G3[r][0] * M[0][k] + G3[r][1] * M[1][k] + G3[r][2] * M[2][k]);
+    double ds[3], dR[3][3];
+    for (int k = 0; k < 3; ++k) {
+        ds[k] = dM[0][k] * Rm[0][k] + dM[1][k] * Rm[1][k] + dM[2][k] * Rm[2][k];
+        for (int r = 0; r < 3; ++r) dR[r][k] = dM[r][k] * sc[k];
+    }
+    // R(q) for the unit quaternion (w, x, y, z)
+    double dqn[4];
+    dqn[0] = 2 * (-qz * dR[0][1] + qy * dR[0][2] + qz * dR[1][0] - qx * dR[1][2] - qy * dR[2][0] + qx * dR[2][1]);
+    dqn[1] = 2 * (qy * dR[0][1] + qz * dR[0][2] + qy * dR[1][0] - 2 * qx * dR[1][1] - qw * dR[1][2] + qz * dR[2][0] +
+                  qw * dR[2][1] - 2 * qx * dR[2][2]);
+    dqn[2] = 2 * (-2 * qy * dR[0][0] + qx * dR[0][1] + qw * dR[0][2] + qx * dR[1][0] + qz * dR[1][2] - qw * dR[2][0] +
+                  qz * dR[2][1] - 2 * qy * dR[2][2]);
+    dqn[3] = 2 * (-2 * qz * dR[0][0] - qw * dR[0][1] + qx * dR[0][2] + qw * dR[1][0] - 2 * qz * dR[1][1] +
+                  qy * dR[1][2] + qx * dR[2][0] + qy * dR[2][1]);
+    const double qn[4] = {qw, qx, qy, qz};
+    double dot = 0;
+    for (int k = 0; k < 4; ++k) dot += qn[k] * dqn[k];
+    double dq[4];
+    for (int k = 0; k < 4; ++k) dq[k] = (dqn[k] - qn[k] * dot) / nq;
+    // SH colour: rgb = max(0, sum_k Y_k h_k + 0.5); dir = (mu - campos)/|mu - campos|
+    double d[3] = {mu[0] - cam.campos[0], mu[1] - cam.campos[1], mu[2] - cam.campos[2]};
+    double len = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double dir[3] = {d[0] / len, d[1] / len, d[2] / len};
+    double Y[16], dY[16][3];
+    sh_basis<double>(dir[0], dir[1], dir[2], Y);
+    sh_basis_grad(dir[0], dir[1], dir[2], dY);
+    const int nc = (s.sh_degree + 1) * (s.sh_degree + 1);
+    double ddir[3] = {0, 0, 0};
+    for (int ch = 0; ch < 3; ++ch) {
+        double raw = 0.5;
+        for (int k = 0; k < nc; ++k) raw += Y[k] * double(s.sh[(k * 3 + ch) * n + i]);
+        const double graw = raw >= 0.0 ? gr.rgb[ch] : 0.0;
+        for (int k = 0; k < nc; ++k) {
+            out[11 + 3 * k + ch] = Y[k] * graw;
+            for (int j = 0; j < 3; ++j) ddir[j] += graw * dY[k][j] * double(s.sh[(k * 3 + ch) * n + i]);
+        }
+    }
+    double dd = dir[0] * ddir[0] + dir[1] * ddir[1] + dir[2] * ddir[2];
+    for (int k = 0; k < 3; ++k) dmu[k] += (ddir[k] - dir[k] * dd) / len;
+    for (int k = 0; k < 3; ++k) out[k] = dmu[k];
+    for (int k = 0; k < 3; ++k) out[3 + k] = ds[k];
+    for (int k = 0; k < 4; ++k) out[6 + k] = dq[k];
+    out[10] = gr.sigma;
+}
+
 void pack_proj(const Proj<double>& P, double* o) {
     o[0] = P.u; o[1] = P.v; o[2] = P.depth; o[3] = P.opacity;
     o[4] = P.a; o[5] = P.b; o[6] = P.c; o[7] = P.t;
@@ -853,6 +1083,63 @@ void oracle_blend_pixel(int prec64, const double* gs, int64_t m, double px, doub
     };
     if (prec64) run(double(0));
     else run(float(0));
+}
+
+// Backward of one tile mode (FP64).  dL_dimage [3][H][W]; grads [59][n]
+// planar (dmu 3, ds 3, dq 4, dsigma 1, dh 48 as [k][ch]); g2d [10][n] =
+// du dv da db dc dsigma dr dg db score (the blend's per-Gaussian sums).
+void oracle_backward(int64_t n, const float* means, const float* scales, const float* rots, const float* opac,
+                     const float* sh, int sh_degree, int width, int height, const float* camf, int tile, int mode,
+                     const float* bg, const double* dL_dimage, double* grads, double* g2d) {
+    SceneIn s{n, sh_degree, means, scales, rots, opac, sh};
+    Cam<double> cam = make_cam<double>(width, height, camf);
+    Grid g = make_grid(width, height, tile);
+    std::vector<Proj<double>> P = preprocess_all<double>(s, cam);
+    std::vector<uint64_t> keys;
+    std::vector<uint32_t> vals;
+    for (int64_t i = 0; i < n; ++i) {
+        float depth_f = static_cast<float>(P[i].depth);
+        uint32_t dbits;
+        std::memcpy(&dbits, &depth_f, 4);
+        mode_tiles<double>(mode, P[i], g, [&](int tx, int ty) {
+            keys.push_back(((uint64_t(ty) * uint64_t(g.gx) + uint64_t(tx)) << 32) | uint64_t(dbits));
+            vals.push_back(static_cast<uint32_t>(i));
+        });
+    }
+    std::vector<int64_t> order(keys.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return keys[a] < keys[b]; });
+    const int64_t G = int64_t(g.gx) * g.gy;
+    std::vector<std::vector<uint32_t>> lists(static_cast<size_t>(G));
+    for (int64_t k : order) lists[keys[k] >> 32].push_back(vals[k]);
+    std::vector<Grad2D> acc(static_cast<size_t>(n));
+    const int64_t HW = int64_t(width) * height;
+    for (int py = 0; py < height; ++py)
+        for (int px = 0; px < width; ++px) {
+            const auto& L = lists[int64_t(py / tile) * g.gx + px / tile];
+            const int64_t o = int64_t(py) * width + px;
+            double Gp[3] = {dL_dimage[o], dL_dimage[HW + o], dL_dimage[2 * HW + o]};
+            blend_backward_pixel(P, L.data(), uint32_t(L.size()), px, py, Gp, bg, acc);
+        }
+    for (int64_t i = 0; i < n; ++i) {
+        double out[59];
+        if (P[i].valid) preprocess_backward_one(s, i, cam, acc[i], out);
+        else for (double& v : out) v = 0.0;
+        for (int k = 0; k < 59; ++k) grads[k * n + i] = out[k];
+        const Grad2D& a = acc[i];
+        const double v2[10] = {a.u, a.v, a.a, a.b, a.c, a.sigma, a.rgb[0], a.rgb[1], a.rgb[2], a.score};
+        for (int k = 0; k < 10; ++k) g2d[k * n + i] = v2[k];
+    }
+}
+
+// SH basis gradient at unit directions dirs[n][3]; out[n][16][3].
+void oracle_sh_basis_grad(const double* dirs, double* out, int64_t n) {
+    for (int64_t i = 0; i < n; ++i) {
+        double dY[16][3];
+        sh_basis_grad(dirs[3 * i], dirs[3 * i + 1], dirs[3 * i + 2], dY);
+        for (int k = 0; k < 16; ++k)
+            for (int j = 0; j < 3; ++j) out[48 * i + 3 * k + j] = dY[k][j];
+    }
 }
 
 }  // extern "C"

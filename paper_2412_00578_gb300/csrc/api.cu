@@ -245,6 +245,27 @@ gs_status gs_render(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* 
     return launch_render(ctx, cfg, v);
 }
 
+gs_status gs_render_stats(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame,
+                          uint64_t* evaluated, uint64_t* contributed, uint64_t* executed) {
+    gs_status st = enter(ctx);
+    if (st) return st;
+    FrameView v;
+    if (!make_view(ctx, frame, &v)) return GS_ERR_INVALID;
+    if ((st = check_cam(ctx, cam, frame)) || (st = check_cfg(ctx, cfg, frame))) return st;
+    unsigned long long* counters = reinterpret_cast<unsigned long long*>(v.status + 4);
+    if (cudaMemsetAsync(counters, 0, 3 * sizeof(unsigned long long), ctx->stream) != cudaSuccess)
+        return set_error(ctx, GS_ERR_CUDA, "render_stats: cudaMemsetAsync failed");
+    if ((st = launch_render(ctx, cfg, v, counters))) return st;
+    unsigned long long h[3] = {0, 0, 0};
+    if (cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        return set_error(ctx, GS_ERR_CUDA, "render_stats: %s", cudaGetErrorString(cudaGetLastError()));
+    if (evaluated) *evaluated = h[0];
+    if (contributed) *contributed = h[1];
+    if (executed) *executed = h[2];
+    return GS_OK;
+}
+
 gs_status gs_forward(gs_context* ctx, const gs_scene* scene, const gs_camera* cam, const gs_raster_cfg* cfg,
                      const gs_frame* frame) {
     gs_status st;
@@ -253,6 +274,27 @@ gs_status gs_forward(gs_context* ctx, const gs_scene* scene, const gs_camera* ca
     if ((st = gs_sort(ctx, cam, cfg, frame))) return st;
     if ((st = gs_tile_ranges(ctx, cam, cfg, frame))) return st;
     return gs_render(ctx, cam, cfg, frame);
+}
+
+int64_t gs_backward_work_bytes(int64_t n_capacity) {
+    return n_capacity < 0 ? 0 : std::max<int64_t>(backward_work_floats(n_capacity) * 4, 4);
+}
+
+gs_status gs_render_backward(gs_context* ctx, const gs_scene* scene, const gs_camera* cam, const gs_raster_cfg* cfg,
+                             const gs_frame* frame, const float* dL_dimage, const gs_grads* grads) {
+    gs_status st = enter(ctx);
+    if (st) return st;
+    FrameView v;
+    if (!make_view(ctx, frame, &v)) return GS_ERR_INVALID;
+    if ((st = check_cam(ctx, cam, frame)) || (st = check_cfg(ctx, cfg, frame))) return st;
+    if (!scene || scene->n < 0 || scene->n > frame->n_capacity)
+        return set_error(ctx, GS_ERR_INVALID, "scene is NULL or larger than the frame");
+    if (!dL_dimage || !grads || !grads->work)
+        return set_error(ctx, GS_ERR_INVALID, "dL_dimage, grads or grads->work is NULL");
+    if (scene->n > 0 && (!scene->means || !scene->scales || !scene->rotations || !scene->sh || !grads->means ||
+                         !grads->scales || !grads->rotations || !grads->opacities || !grads->sh))
+        return set_error(ctx, GS_ERR_INVALID, "scene or grads has a NULL array");
+    return launch_backward(ctx, scene, cam, cfg, v, dL_dimage, grads);
 }
 
 gs_status gs_read_status(gs_context* ctx, const gs_frame* frame, int64_t* num_keys, uint32_t* flags) {

@@ -20,6 +20,7 @@ constexpr int kMaxTile = 32;
 // ---------------------------------------------------------------- status words
 // scratch layout starts with these words (device):
 //   [0] key total K, low 32 bits   [1] K high bits   [2] GS_FLAG_* bits
+//   [4..9] three 64-bit counters of the instrumented blend (gs_render_stats)
 constexpr int kStatusWords = 16;
 
 struct FrameView {
@@ -47,11 +48,11 @@ struct FrameView {
 
 // ---------------------------------------------------------------- scan / sort geometry
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 16;  // counts per thread
+constexpr int kScanItems = 4;  // counts per thread (rounds per emit block)
 constexpr int kScanBlock = kScanThreads * kScanItems;
 
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortThreads = 512;
+constexpr int kSortItems = 8;
 constexpr int kSortPartition = kSortThreads * kSortItems;  // keys per onesweep partition
 constexpr int kMaxPasses = 8;
 
@@ -147,5 +148,9 @@ gs_status launch_preprocess(gs_context* ctx, const gs_scene* s, const gs_camera*
 gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v);
 gs_status launch_sort(gs_context* ctx, const FrameView& v);
 gs_status launch_ranges(gs_context* ctx, const FrameView& v);
-gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v);
+gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v,
+                        unsigned long long* stats = nullptr);
+gs_status launch_backward(gs_context* ctx, const gs_scene* s, const gs_camera* cam, const gs_raster_cfg* cfg,
+                          const FrameView& v, const float* dL_dimg, const gs_grads* g);
+int64_t backward_work_floats(int64_t ncap);
 }  // namespace gs

@@ -1,13 +1,13 @@
 // InclusiveSum + duplicateWithKeys (Sec. 3.2.2).
 //
 // Three launches:
-//   scan_reduce  each block sums 4096 tile counts (int64 partial per block);
+//   scan_reduce  each block sums 1024 tile counts (int64 partial per block);
 //   scan_top     one block turns the partials into exclusive block offsets,
 //                stores the key total K in the frame status and flags a
 //                capacity overflow;
-//   emit         each block re-reads its 4096 counts, scans them in shared
-//                memory (so per-Gaussian offsets are never stored in HBM),
-//                and every Gaussian with tiles recomputes its tile set with
+//   emit         each block re-reads its 1024 counts, scans them in shared
+//                memory round by round (so per-Gaussian offsets are never
+//                stored in HBM), and every Gaussian with tiles recomputes its tile set with
 //                the same localization function the count used and writes
 //                its (tile << 32 | depth bits, index) pairs at its offset.
 #include "tiles.cuh"
@@ -134,23 +134,22 @@ struct KeyWriter {
 __global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
     __shared__ long long s_warp[32];
     if (A.status[2] & GS_FLAG_CAPACITY) return;  // keys do not fit: emit nothing
-    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
-    int c[kScanItems];
-    long long sum = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int64_t i = base + k;
-        c[k] = i < A.n ? A.counts[i] : 0;
-        sum += c[k];
-    }
-    long long total;
-    long long off = block_excl_scan(sum, s_warp, &total) + A.partials[blockIdx.x];
+    // The block's 1024 Gaussians are taken in 4 rounds of 256 consecutive
+    // ones (one per thread), so the 2D-state loads of a round are coalesced
+    // and neighbouring threads write neighbouring key ranges.
+    long long carry = A.partials[blockIdx.x];
+    const int64_t block0 = (int64_t)blockIdx.x * kScanBlock;
 #pragma unroll 1
-    for (int k = 0; k < kScanItems; ++k) {
-        if (c[k] == 0) continue;
-        const int64_t i = base + k;
+    for (int r = 0; r < kScanItems; ++r) {
+        const int64_t i = block0 + (int64_t)r * kScanThreads + threadIdx.x;
+        const int c = i < A.n ? A.counts[i] : 0;
+        long long total;
+        const long long off = carry + block_excl_scan(c, s_warp, &total);
+        __syncthreads();  // s_warp is reused by the next round's scan
+        carry += total;
+        if (c == 0) continue;
         const float4 q0 = A.p0[i];
-        KeyWriter W{A.keys, A.vals, off, off + c[k], __float_as_uint(q0.w), (uint32_t)i, A.grid.gx};
+        KeyWriter W{A.keys, A.vals, off, off + c, __float_as_uint(q0.w), (uint32_t)i, A.grid.gx};
         if (A.mode == GS_MODE_3SIGMA) {
             Rect R;
             if (sigma3_rect(q0.x, q0.y, __float_as_int(A.p2[i].w), A.grid, R))
@@ -169,7 +168,6 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
                 }
             }
         }
-        off += c[k];
     }
 }
 

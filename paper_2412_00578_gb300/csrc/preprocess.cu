@@ -70,7 +70,7 @@ __device__ __forceinline__ void sh_basis16(float x, float y, float z, float Y[16
     Y[15] = ((-kC3a) * x) * (xx - 3.0f * yy);
 }
 
-__global__ void __launch_bounds__(256) preprocess_kernel(const PreArgs A) {
+__global__ void __launch_bounds__(256, 4) preprocess_kernel(const PreArgs A) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.ncap) return;
     int count = 0;
@@ -171,9 +171,16 @@ __global__ void __launch_bounds__(256) preprocess_kernel(const PreArgs A) {
                         float rgb[3];
 #pragma unroll
                         for (int ch = 0; ch < 3; ++ch) {
-                            float acc = Y[0] * __ldg(A.sh + (int64_t)ch * n + i);
-                            for (int k = 1; k < A.sh_coeffs; ++k)
-                                acc = acc + Y[k] * __ldg(A.sh + (int64_t)(k * 3 + ch) * n + i);
+                            // issue all of the channel's coefficient loads before
+                            // accumulating (same summation order as a plain loop)
+                            float h[16];
+#pragma unroll
+                            for (int k = 0; k < 16; ++k)
+                                h[k] = k < A.sh_coeffs ? __ldg(A.sh + (int64_t)(k * 3 + ch) * n + i) : 0.0f;
+                            float acc = Y[0] * h[0];
+#pragma unroll
+                            for (int k = 1; k < 16; ++k)
+                                if (k < A.sh_coeffs) acc = acc + Y[k] * h[k];
                             acc = acc + 0.5f;
                             rgb[ch] = acc < 0.0f ? 0.0f : acc;
                         }

@@ -3,17 +3,22 @@
 // ranges: one thread per sorted key; a thread whose tile differs from its
 // predecessor's closes the previous range and opens its own.
 //
-// blend: one CTA per tile, one thread per pixel.  The tile's Gaussians are
-// brought into shared memory in batches of one per thread (a gather of the
-// 48-byte 2D state by sorted index), then every pixel walks the batch in
-// depth order.  Per pixel (Eqs. render_alpha, 2d_gaussian_scalar,
+// blend: one CTA per tile, one thread per pixel, each warp owning an 8 x 4
+// pixel sub-tile.  The tile's Gaussians are brought into shared memory in
+// batches of one per thread (a gather of the 48-byte 2D state by sorted
+// index); the loading thread also computes which sub-tiles the Gaussian's
+// ellipse can reach, and each warp then walks, in depth order, only the
+// Gaussians whose mask has its bit (ballot + find-first-set), so warps skip
+// the many tile entries that lie elsewhere in the tile.  Every pixel still
+// evaluates every Gaussian that can reach it in the same order with the same
+// arithmetic.  Per pixel (Eqs. render_alpha, 2d_gaussian_scalar,
 // contribution): dx = px - u, dy = py - v, e = (2b) dy, f = (c dy) dy,
 // q = fma(dx, fma(a, dx, e), f); a Gaussian counts iff q <= t (alpha >= 1/255);
 // alpha = min(0.99, sigma exp(-q/2)); T' = T (1 - alpha); if T' < 1e-4 the
 // pixel stops before adding it; else C = fma(c, alpha T, C), T = T'.
 // The CTA leaves the loop as soon as every pixel has stopped
 // (__syncthreads_count vote before each batch).
-#include "gs_common.cuh"
+#include "blend_common.cuh"
 
 namespace gs {
 namespace {
@@ -51,41 +56,54 @@ struct BlendArgs {
     uint32_t* last;
     int width, height, gx;
     float bg0, bg1, bg2;
+    unsigned long long* stats;  // [3]: defined, contributing, executed pair counts (stats variant)
 };
 
-template <int T>
-__global__ void __launch_bounds__(T* T) blend_kernel(const BlendArgs A) {
+template <int T, bool kStats>
+__global__ void __launch_bounds__(T* T, T == 32 ? 1 : 2) blend_kernel(const BlendArgs A) {
     constexpr int NT = T * T;
-    __shared__ float4 s_g0[NT];  // u, v, a, 2b
-    __shared__ float4 s_g1[NT];  // c, t, opacity, -
-    __shared__ float4 s_g2[NT];  // r, g, b, -
+    constexpr int NB = NT < 256 ? NT : 256;  // Gaussians per shared-memory batch
+    constexpr int NSX = T / kSubW;
+    __shared__ float4 s_g0[NB];  // u, v, a, 2b
+    __shared__ float4 s_g1[NB];  // c, t, opacity, -
+    __shared__ float4 s_g2[NB];  // r, g, b, -
+    __shared__ uint32_t s_mask[NB];
     const int tile = blockIdx.x;
     const int tx = tile % A.gx, ty = tile / A.gx;
-    const int px = tx * T + (int)(threadIdx.x % T);
-    const int py = ty * T + (int)(threadIdx.x / T);
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const uint32_t my_bit = 1u << warp;
+    const int px = tx * T + (warp % NSX) * kSubW + (lane & (kSubW - 1));
+    const int py = ty * T + (warp / NSX) * kSubH + (lane >> 3);
     const bool inside = px < A.width && py < A.height;
     const float pxf = (float)px, pyf = (float)py;
+    const float ox = (float)(tx * T), oy = (float)(ty * T);
     const uint2 rg = A.ranges[tile];
     const int n = (int)(rg.y - rg.x);
     float Tr = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     uint32_t last = 0;
     bool done = !inside;
-    for (int b0 = 0; b0 < n; b0 += NT) {
+    uint32_t stop_pos = 0, n_exec = 0, n_contrib = 0;
+    for (int b0 = 0; b0 < n; b0 += NB) {
         if (__syncthreads_count(done) == NT) break;
         const int j = b0 + (int)threadIdx.x;
-        if (j < n) {
+        if ((int)threadIdx.x < NB && j < n) {
             const uint32_t id = A.vals[rg.x + j];
             const float4 q0 = A.p0[id];
             const float4 q1 = A.p1[id];
-            const float4 q2 = A.p2[id];
             s_g0[threadIdx.x] = make_float4(q0.x, q0.y, q1.x, q1.y + q1.y);
             s_g1[threadIdx.x] = make_float4(q1.z, q1.w, q0.z, 0.0f);
-            s_g2[threadIdx.x] = q2;
+            s_g2[threadIdx.x] = A.p2[id];
+            s_mask[threadIdx.x] = subtile_mask<T>(q0.x, q0.y, q1.x, q1.y, q1.z, q1.w, ox, oy);
         }
         __syncthreads();
-        if (!done) {
-            const int cnt = min(NT, n - b0);
-            for (int k = 0; k < cnt; ++k) {
+        const int cnt = min(NB, n - b0);
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            if (__all_sync(0xffffffffu, done)) break;
+            uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && (s_mask[c0 + lane] & my_bit));
+            while (bits) {
+                const int k = c0 + __ffs(bits) - 1;
+                bits &= bits - 1u;
+                if (done) continue;
                 const float4 g0 = s_g0[k];
                 const float4 g1 = s_g1[k];
                 const float dx = pxf - g0.x;
@@ -93,21 +111,24 @@ __global__ void __launch_bounds__(T* T) blend_kernel(const BlendArgs A) {
                 const float e = g0.w * dy;
                 const float f = (g1.x * dy) * dy;
                 const float q = fmaf(dx, fmaf(g0.z, dx, e), f);
+                if (kStats) ++n_exec;
                 if (!(q <= g1.y)) continue;
                 const float g = gs_expf(-0.5f * q);
                 const float alpha = fminf(0.99f, g1.z * g);
                 const float Tn = Tr * (1.0f - alpha);
                 if (Tn < 1e-4f) {
                     done = true;
-                    break;
+                    stop_pos = (uint32_t)(b0 + k + 1);
+                    continue;
                 }
                 const float w = alpha * Tr;
-                const float4 c = s_g2[k];
-                C0 = fmaf(c.x, w, C0);
-                C1 = fmaf(c.y, w, C1);
-                C2 = fmaf(c.z, w, C2);
+                const float4 col = s_g2[k];
+                C0 = fmaf(col.x, w, C0);
+                C1 = fmaf(col.y, w, C1);
+                C2 = fmaf(col.z, w, C2);
                 Tr = Tn;
                 last = (uint32_t)(b0 + k + 1);
+                if (kStats) ++n_contrib;
             }
         }
     }
@@ -119,6 +140,18 @@ __global__ void __launch_bounds__(T* T) blend_kernel(const BlendArgs A) {
         A.image[2 * HW + o] = fmaf(Tr, A.bg2, C2);
         A.final_T[o] = Tr;
         A.last[o] = last;
+    }
+    if (kStats) {
+        // pairs the tile-list definition evaluates: every entry up to the stop
+        const uint32_t n_def = !inside ? 0u : (stop_pos ? stop_pos : (uint32_t)n);
+        const uint32_t e = __reduce_add_sync(0xffffffffu, n_def);
+        const uint32_t c = __reduce_add_sync(0xffffffffu, n_contrib);
+        const uint32_t x = __reduce_add_sync(0xffffffffu, n_exec);
+        if (lane == 0) {
+            atomicAdd(A.stats, (unsigned long long)e);
+            atomicAdd(A.stats + 1, (unsigned long long)c);
+            atomicAdd(A.stats + 2, (unsigned long long)x);
+        }
     }
 }
 
@@ -135,7 +168,7 @@ gs_status launch_ranges(gs_context* ctx, const FrameView& v) {
     return check_launch(ctx, "tile_ranges");
 }
 
-gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v) {
+gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v, unsigned long long* stats) {
     BlendArgs A;
     A.ranges = v.ranges;
     A.vals = v.vals0;
@@ -151,13 +184,23 @@ gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameVi
     A.bg0 = cfg->bg[0];
     A.bg1 = cfg->bg[1];
     A.bg2 = cfg->bg[2];
+    A.stats = stats;
     const unsigned tiles = (unsigned)(v.gx * v.gy);
     if (tiles == 0) return GS_OK;
-    switch (v.tile) {
-        case 8: blend_kernel<8><<<tiles, 64, 0, ctx->stream>>>(A); break;
-        case 16: blend_kernel<16><<<tiles, 256, 0, ctx->stream>>>(A); break;
-        case 32: blend_kernel<32><<<tiles, 1024, 0, ctx->stream>>>(A); break;
-        default: return set_error(ctx, GS_ERR_INVALID, "render: tile %d not supported", v.tile);
+    if (stats) {
+        switch (v.tile) {
+            case 8: blend_kernel<8, true><<<tiles, 64, 0, ctx->stream>>>(A); break;
+            case 16: blend_kernel<16, true><<<tiles, 256, 0, ctx->stream>>>(A); break;
+            case 32: blend_kernel<32, true><<<tiles, 1024, 0, ctx->stream>>>(A); break;
+            default: return set_error(ctx, GS_ERR_INVALID, "render: tile %d not supported", v.tile);
+        }
+    } else {
+        switch (v.tile) {
+            case 8: blend_kernel<8, false><<<tiles, 64, 0, ctx->stream>>>(A); break;
+            case 16: blend_kernel<16, false><<<tiles, 256, 0, ctx->stream>>>(A); break;
+            case 32: blend_kernel<32, false><<<tiles, 1024, 0, ctx->stream>>>(A); break;
+            default: return set_error(ctx, GS_ERR_INVALID, "render: tile %d not supported", v.tile);
+        }
     }
     ctx->launches += 1;
     return check_launch(ctx, "render");

@@ -30,6 +30,7 @@ constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr uint32_t kNoDigit = 0xffffffffu;
+constexpr int kLookWindow = 8;  // predecessors inspected per look-back step
 
 __device__ __forceinline__ uint32_t frame_keys(const uint32_t* status) {
     return (status[2] & GS_FLAG_CAPACITY) ? 0u : status[0];
@@ -62,9 +63,10 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const HistArgs A) {
         if (sh[i]) atomicAdd(&A.hist[i], sh[i]);
 }
 
-// Exclusive scan of one value per thread over a 256-thread block.
+// Exclusive scan of one value per thread over the block (up to 1024 threads).
 __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* s_warp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (int)(blockDim.x >> 5);
     uint32_t inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -74,13 +76,13 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* s_
     if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = lane < 8 ? s_warp[lane] : 0u;
+        uint32_t w = lane < nwarps ? s_warp[lane] : 0u;
 #pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
+        for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += y;
         }
-        if (lane < 8) s_warp[lane] = w;
+        if (lane < nwarps) s_warp[lane] = w;
     }
     __syncthreads();
     const uint32_t r = (warp > 0 ? s_warp[warp - 1] : 0u) + inc - v;
@@ -111,7 +113,7 @@ struct PassSmem {
     uint32_t part;
 };
 
-__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(const PassArgs A) {
+__global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PassSmem& S = *reinterpret_cast<PassSmem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -125,8 +127,9 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(const PassArgs 
     const uint32_t base = part * kSortPartition;
     const uint32_t mask = (1u << A.dbits) - 1u;
 
-    // Load: warp w owns keys [base + 512 w, base + 512 (w+1)); round r reads
-    // 32 consecutive keys, so (warp, round, lane) order is input order.
+    // Load: warp w owns keys [base + 32 I w, base + 32 I (w+1)) (I items per
+    // thread); round r reads 32 consecutive keys, so (warp, round, lane) order
+    // is input order.
     uint64_t key[kSortItems];
     uint32_t val[kSortItems];
     uint32_t rank[kSortItems];
@@ -152,45 +155,66 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(const PassArgs 
         __syncwarp();
     }
     __syncthreads();
-    // Per digit (thread t <-> digit t): warp-exclusive offsets and block total.
+    // Per digit (threads 0..255, thread t <-> digit t): warp-exclusive offsets,
+    // block total, look-back.  The other threads feed zeros to the block scans.
     const uint32_t t = tid;
+    const bool digit_thread = t < 256;
     uint32_t tot = 0;
+    if (digit_thread) {
 #pragma unroll
-    for (int w = 0; w < kSortThreads / 32; ++w) {
-        const uint32_t c = S.wcnt[w][t];
-        S.wcnt[w][t] = tot;
-        tot += c;
-    }
-    uint32_t* my = A.lookback + (size_t)part * 256 + t;
-    st_relaxed_gpu(my, (part == 0 ? kFlagPrefix : kFlagAgg) | tot);
-    // clear this partition's row of the next pass's table (that table's last
-    // user was the previous pass, which has completed)
-    if (A.lookback_next) A.lookback_next[(size_t)part * 256 + t] = 0;
-    const uint32_t boff = block_excl_scan_u32(tot, S.warp_tmp);
-    const uint32_t dstart = block_excl_scan_u32(A.hist[t], S.warp_tmp);
-    uint32_t prefix = 0;
-    if (part > 0) {
-        int64_t j = (int64_t)part - 1;
-        uint32_t spins = 0;
-        while (j >= 0) {
-            const uint32_t w = ld_relaxed_gpu(A.lookback + (size_t)j * 256 + t);
-            const uint32_t flag = w & ~kCountMask;
-            if (flag == 0) {
-                if (++spins > kSpinLimit) {
-                    atomicOr(A.status + 2, GS_FLAG_TIMEOUT);
-                    break;
-                }
-                __nanosleep(32);
-                continue;
-            }
-            prefix += w & kCountMask;
-            if (flag == kFlagPrefix) break;
-            --j;
+        for (int w = 0; w < kSortThreads / 32; ++w) {
+            const uint32_t c = S.wcnt[w][t];
+            S.wcnt[w][t] = tot;
+            tot += c;
         }
-        st_relaxed_gpu(my, kFlagPrefix | (prefix + tot));
+        st_relaxed_gpu(A.lookback + (size_t)part * 256 + t, (part == 0 ? kFlagPrefix : kFlagAgg) | tot);
+        // clear this partition's row of the next pass's table (that table's last
+        // user was the previous pass, which has completed)
+        if (A.lookback_next) A.lookback_next[(size_t)part * 256 + t] = 0;
     }
-    S.boff[t] = boff;
-    S.gbase[t] = dstart + prefix - boff;  // modular: gbase + staging index = output index
+    const uint32_t boff = block_excl_scan_u32(tot, S.warp_tmp);
+    const uint32_t dstart = block_excl_scan_u32(digit_thread ? A.hist[t] : 0u, S.warp_tmp);
+    if (digit_thread) {
+        uint32_t prefix = 0;
+        if (part > 0) {
+            // Look back over the predecessors' published words, kLookWindow at
+            // a time (all loads in flight together): add aggregates until an
+            // inclusive prefix is found; on a word not yet published, poll it
+            // again (bounded).
+            int64_t j = (int64_t)part - 1;
+            uint32_t spins = 0;
+            bool found = false;
+            while (!found && j >= 0) {
+                uint32_t w[kLookWindow];
+#pragma unroll
+                for (int m = 0; m < kLookWindow; ++m)
+                    w[m] = (j - m >= 0) ? ld_relaxed_gpu(A.lookback + (size_t)(j - m) * 256 + t) : kFlagPrefix;
+                int m = 0;  // words consumed from this window
+#pragma unroll
+                for (int mm = 0; mm < kLookWindow; ++mm) {
+                    const uint32_t flag = w[mm] & ~kCountMask;
+                    if (flag == 0) break;  // not yet published: poll again from here
+                    prefix += w[mm] & kCountMask;
+                    ++m;
+                    if (flag == kFlagPrefix) {
+                        found = true;
+                        break;
+                    }
+                }
+                j -= m;
+                if (!found && m < kLookWindow && j >= 0) {
+                    if (++spins > kSpinLimit) {
+                        atomicOr(A.status + 2, GS_FLAG_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            st_relaxed_gpu(A.lookback + (size_t)part * 256 + t, kFlagPrefix | (prefix + tot));
+        }
+        S.boff[t] = boff;
+        S.gbase[t] = dstart + prefix - boff;  // modular: gbase + staging index = output index
+    }
     __syncthreads();
     // Stage in digit order.
 #pragma unroll

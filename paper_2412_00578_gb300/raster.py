@@ -52,14 +52,19 @@ class GsFrame(ctypes.Structure):
                 ("last", c_void_p), ("scratch", c_void_p)]
 
 
+class GsGrads(ctypes.Structure):
+    _fields_ = [(k, c_void_p) for k in ("means", "scales", "rotations", "opacities", "sh", "means2d", "score",
+                                        "work")]
+
+
 class GsFrameBytes(ctypes.Structure):
     _fields_ = [(k, c_int64) for k in ("proj", "counts", "keys", "vals", "ranges", "image", "final_T", "last",
                                        "scratch")]
 
 
 EXPORTS = ["gs_create", "gs_destroy", "gs_set_stream", "gs_last_error", "gs_launch_count", "gs_frame_sizes",
-           "gs_preprocess", "gs_intersect", "gs_sort", "gs_tile_ranges", "gs_render", "gs_forward",
-           "gs_read_status"]
+           "gs_preprocess", "gs_intersect", "gs_sort", "gs_tile_ranges", "gs_render", "gs_render_stats",
+           "gs_forward", "gs_read_status", "gs_backward_work_bytes", "gs_render_backward"]
 
 _lib = None
 
@@ -90,8 +95,14 @@ def load(path=None) -> ctypes.CDLL:
         getattr(L, name).argtypes = [P, POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame)]
     L.gs_forward.argtypes = [P, POINTER(GsScene), POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame)]
     L.gs_read_status.argtypes = [P, POINTER(GsFrame), POINTER(c_int64), POINTER(c_uint32)]
+    L.gs_render_stats.argtypes = [P, POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame),
+                                  POINTER(ctypes.c_uint64), POINTER(ctypes.c_uint64), POINTER(ctypes.c_uint64)]
+    L.gs_backward_work_bytes.argtypes = [c_int64]
+    L.gs_render_backward.argtypes = [P, POINTER(GsScene), POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame),
+                                     P, POINTER(GsGrads)]
     for name in EXPORTS:
         getattr(L, name).restype = ctypes.c_int
+    L.gs_backward_work_bytes.restype = c_int64
     L.gs_destroy.restype = None
     L.gs_last_error.restype = ctypes.c_char_p
     L.gs_launch_count.restype = c_int64
@@ -181,6 +192,8 @@ class Frame:
     def unsorted_pairs(self, K: int):
         return self.keys[:K], self.vals[:K]
 
+    generation = 0  # bumped by every forward render into this frame
+
     def tile_ranges(self):
         return self.ranges[: self.gx * self.gy * 2].view(self.gx * self.gy, 2)
 
@@ -257,6 +270,31 @@ class Rasterizer:
         self._check(self.lib.gs_render(self.ctx, ctypes.byref(c), ctypes.byref(cfg), ctypes.byref(frame.struct)),
                     "gs_render")
 
+    def gs_render_stats(self, cam, cfg, frame: Frame):
+        """Instrumented blend: (pairs the definition evaluates, contributing pairs, pairs executed)."""
+        c = camera_struct(cam)
+        ev, co, ex = ctypes.c_uint64(0), ctypes.c_uint64(0), ctypes.c_uint64(0)
+        self._check(self.lib.gs_render_stats(self.ctx, ctypes.byref(c), ctypes.byref(cfg), ctypes.byref(frame.struct),
+                                             ctypes.byref(ev), ctypes.byref(co), ctypes.byref(ex)), "gs_render_stats")
+        return int(ev.value), int(co.value), int(ex.value)
+
+    def gs_render_backward(self, scene, cam, cfg, frame: Frame, dL_dimage: torch.Tensor, grads: dict,
+                           work: torch.Tensor):
+        """grads: dict of CUDA float32 tensors shaped like the scene arrays
+        (means, scales, rotations, opacities, sh), optional means2d (2, n)
+        and score (n,) (added to)."""
+        s, c = scene_struct(scene), camera_struct(cam)
+        if not (dL_dimage.is_cuda and dL_dimage.dtype == torch.float32 and dL_dimage.is_contiguous()):
+            raise ValueError("dL_dimage must be a contiguous float32 CUDA tensor of shape (3, H, W)")
+        g = GsGrads()
+        for k in ("means", "scales", "rotations", "opacities", "sh", "means2d", "score"):
+            t = grads.get(k)
+            setattr(g, k, t.data_ptr() if t is not None else None)
+        g.work = work.data_ptr()
+        self._check(self.lib.gs_render_backward(self.ctx, ctypes.byref(s), ctypes.byref(c), ctypes.byref(cfg),
+                                                ctypes.byref(frame.struct), c_void_p(dL_dimage.data_ptr()),
+                                                ctypes.byref(g)), "gs_render_backward")
+
     def gs_forward(self, scene, cam, cfg, frame: Frame):
         s, c = scene_struct(scene), camera_struct(cam)
         self._check(self.lib.gs_forward(self.ctx, ctypes.byref(s), ctypes.byref(c), ctypes.byref(cfg),
@@ -307,6 +345,7 @@ class Renderer:
         n = int(scene.means.shape[1])
         f = self.frame(n, cam.width, cam.height, tile)
         r = self.rast
+        f.generation += 1
         r.gs_preprocess(scene, cam, cfg, f)
         r.gs_intersect(cam, cfg, f)
         r.gs_sort(cam, cfg, f)
@@ -317,6 +356,7 @@ class Renderer:
             if K > MAX_KEYS:
                 raise GsError(3, f"{K} keys exceed the library maximum {MAX_KEYS}")
             f = self.frame(n, cam.width, cam.height, tile, min_keys=int(K * self.headroom) + 1)
+            f.generation += 1
             r.gs_preprocess(scene, cam, cfg, f)
             r.gs_intersect(cam, cfg, f)
             r.gs_sort(cam, cfg, f)
@@ -326,3 +366,73 @@ class Renderer:
         if flags:
             r.gs_read_status(f, raise_on_error=True)
         return RenderOutput(f.image, f.final_T, f.last, K, f)
+
+
+def backward_work_bytes(n: int) -> int:
+    return int(load().gs_backward_work_bytes(int(n)))
+
+
+class SceneView:
+    """Scene arrays as a plain object (the layout of synth.Scene)."""
+
+    def __init__(self, means, scales, rotations, opacities, sh, sh_degree=3):
+        self.means, self.scales, self.rotations, self.opacities, self.sh = means, scales, rotations, opacities, sh
+        self.sh_degree = sh_degree
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, scales, rotations, opacities, sh, diff, cam, mode, tile, bg, sh_degree):
+        scene = SceneView(means.detach().contiguous(), scales.detach().contiguous(), rotations.detach().contiguous(),
+                          opacities.detach().contiguous(), sh.detach().contiguous(), sh_degree)
+        out = diff.renderer.render(scene, cam, mode, tile, bg)
+        ctx.diff, ctx.cam, ctx.cfg = diff, cam, cfg_struct(tile, mode, bg)
+        ctx.frame, ctx.generation, ctx.scene = out.frame, out.frame.generation, scene
+        return out.image.clone()
+
+    @staticmethod
+    def backward(ctx, grad_image):
+        f = ctx.frame
+        if f.generation != ctx.generation:
+            raise RuntimeError("the frame was re-rendered before backward; call backward before the next forward "
+                               "of the same size")
+        sc = ctx.scene
+        n = sc.means.shape[1]
+        diff = ctx.diff
+        grads = {k: torch.empty_like(getattr(sc, k)) for k in ("means", "scales", "rotations", "opacities", "sh")}
+        grads["means2d"] = torch.empty(2, n, dtype=torch.float32, device=sc.means.device)
+        if diff.score is not None:
+            grads["score"] = diff.score
+        work = diff.work(f.n, sc.means.device)
+        diff.renderer.rast.gs_render_backward(sc, ctx.cam, ctx.cfg, f, grad_image.contiguous().float(), grads, work)
+        diff.means2d_grad = grads["means2d"]
+        return (grads["means"], grads["scales"], grads["rotations"], grads["opacities"], grads["sh"], None, None, None,
+                None, None, None)
+
+
+class DiffRenderer:
+    """Differentiable forward render (torch.autograd) over the CUDA library.
+
+    ``render(means, scales, rotations, opacities, sh, cam)`` returns the
+    (3, H, W) image; its backward runs gs_render_backward.  If ``score`` is a
+    (N,) tensor, each backward adds the efficient pruning score to it.  The
+    frame is reused per raster size, so call backward before the next forward
+    of the same size (checked).
+    """
+
+    def __init__(self, device=None, mode="accutile", tile=16, bg=(0.0, 0.0, 0.0)):
+        self.renderer = Renderer(device)
+        self.mode, self.tile, self.bg = mode, tile, bg
+        self.score = None
+        self.means2d_grad = None
+        self._work = None
+
+    def work(self, n, device):
+        need = backward_work_bytes(n) // 4
+        if self._work is None or self._work.numel() < need:
+            self._work = torch.empty(need, dtype=torch.float32, device=device)
+        return self._work
+
+    def render(self, means, scales, rotations, opacities, sh, cam, sh_degree=3):
+        return _RenderFn.apply(means, scales, rotations, opacities, sh, self, cam, self.mode, self.tile, self.bg,
+                               sh_degree)

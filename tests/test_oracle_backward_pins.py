@@ -1,0 +1,121 @@
+"""Pins of the oracle's analytic backward (FP64) against central finite
+differences of the oracle's own FP64 forward (a different code path: the
+forward never differentiates), the SH basis derivative against finite
+differences of the basis, and the pruning score against its closed form."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_00578_gb300 import synth
+
+
+def tiny_scene(n=40, seed=50, w=48, h=40):
+    scene = synth.uniform_box_scene(n, seed=seed, half=1.0, log_scale_mu=-2.5, log_scale_sd=0.4)
+    cam = synth.look_at(w, h, 60.0, (0.4, -0.3, -4.0), (0.0, 0.0, 0.0))
+    return scene, cam
+
+
+def as_np(scene):
+    d = {k: np.array(getattr(scene, k).numpy(), copy=True) for k in ("means", "scales", "rotations", "opacities", "sh")}
+    return d
+
+
+class NpScene:
+    def __init__(self, d, deg=3):
+        for k, v in d.items():
+            setattr(self, k, v)
+        self.sh_degree = deg
+
+
+def loss(d, cam, W, tile, mode, bg):
+    img = oracle.render(NpScene(d), cam, tile, mode, bg=bg, prec64=True)["image"]
+    return float((W * img).sum())
+
+
+def fd_grad(d, cam, W, key, idx, tile, mode, bg, rel):
+    x0 = d[key][idx]
+    h = max(abs(float(x0)) * rel, 1e-4)
+    vals = []
+    for step in (h, h / 2):
+        dp = {k: v.copy() for k, v in d.items()}
+        dm = {k: v.copy() for k, v in d.items()}
+        dp[key][idx] = np.float32(x0 + step)
+        dm[key][idx] = np.float32(x0 - step)
+        he = (float(dp[key][idx]) - float(dm[key][idx])) / 2
+        vals.append((loss(dp, cam, W, tile, mode, bg) - loss(dm, cam, W, tile, mode, bg)) / (2 * he))
+    return vals
+
+
+@pytest.mark.parametrize("mode", [2, 0])
+def test_backward_matches_finite_differences(mode):
+    scene, cam = tiny_scene()
+    d = as_np(scene)
+    rng = np.random.default_rng(51)
+    W = rng.normal(size=(3, cam.height, cam.width))
+    bg = (0.2, 0.1, 0.3)
+    grads, g2d = oracle.backward(scene, cam, W, 16, mode, bg)
+    contributing = np.nonzero(np.abs(g2d[:6]).sum(0) > 0)[0]
+    assert len(contributing) > 10
+    scale = {k: np.sqrt(np.mean(np.square(v))) for k, v in grads.items()}
+    checked = skipped = 0
+    for trial in range(120):
+        i = int(rng.choice(contributing))
+        key = ["means", "scales", "rotations", "opacities", "sh"][trial % 5]
+        if key == "means":
+            idx = (int(rng.integers(3)), i)
+        elif key == "scales":
+            idx = (int(rng.integers(3)), i)
+        elif key == "rotations":
+            idx = (int(rng.integers(4)), i)
+        elif key == "opacities":
+            idx = (i,)
+        else:
+            idx = (int(rng.integers(16)), int(rng.integers(3)), i)
+        f1, f2 = fd_grad(d, cam, W, key, idx, 16, mode, bg, 2e-3)
+        if abs(f1 - f2) > 1e-3 * max(abs(f1), abs(f2), scale[key]):
+            skipped += 1  # the perturbation crossed a threshold, clamp or stop decision
+            continue
+        g = float(grads[key][idx])
+        denom = max(abs(f2), 1e-3 * scale[key], 1e-12)
+        assert abs(g - f2) / denom <= 2e-3, (key, idx, g, f2)
+        checked += 1
+    assert checked >= 64, (checked, skipped)
+
+
+def test_sh_basis_gradient_against_finite_differences():
+    rng = np.random.default_rng(52)
+    d = rng.normal(size=(200, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    G = oracle.sh_basis_grad(d)
+    h = 1e-6
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = h
+        fd = (oracle.sh_basis(d + e) - oracle.sh_basis(d - e)) / (2 * h)  # derivative of the polynomial form
+        np.testing.assert_allclose(G[:, :, j], fd, atol=1e-7)
+
+
+def test_pruning_score_single_gaussian_closed_form():
+    """One Gaussian, bg = 0, colour c: C = c alpha, dC/dg = sigma c wherever
+    sigma g < 0.99 and q <= t, so score = sigma^2 |c|^2 #{such pixels}."""
+    scene = synth.uniform_box_scene(1, seed=53)
+    scene.means[:] = 0.0
+    scene.scales[:] = 0.02
+    scene.opacities[:] = 0.6
+    scene.sh[:] = 0.0
+    scene.sh[0] = 1.0  # colour = C0 + 0.5 per channel
+    cam = synth.pinhole(32, 32, 60.0, np.eye(3), np.array([0.0, 0.0, 3.0]))
+    W = np.zeros((3, 32, 32))
+    _, g2d = oracle.backward(scene, cam, W, 16, 2)
+    st, _ = oracle.preprocess(scene, cam, 16, 2, prec64=True)
+    u, v, a, b, c, t = st[0, [0, 1, 4, 5, 6, 7]]
+    col = st[0, 8:11]
+    X, Y = np.meshgrid(np.arange(32.0), np.arange(32.0))
+    dx, dy = X - u, Y - v
+    q = a * dx * dx + 2 * b * dx * dy + c * dy * dy
+    sig = float(np.float32(0.6))
+    inside = (q <= t) & (sig * np.exp(-q / 2) < 0.99)
+    assert inside.sum() > 5
+    assert g2d[9, 0] == pytest.approx(sig * sig * float((col ** 2).sum()) * inside.sum(), rel=1e-12)
