@@ -1,0 +1,167 @@
+"""Backward pass (render backward, preprocess backward, pruning score) of the
+CUDA path against the FP64 oracle gradients (themselves pinned by finite
+differences in test_oracle_backward_pins.py), plus finite differences of the
+GPU forward and the torch.autograd wrapper."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2412_00578_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("means", "scales", "rotations", "opacities", "sh")
+
+
+@pytest.fixture(scope="module")
+def raster():
+    from paper_2412_00578_gb300 import build
+
+    build.build()
+    from paper_2412_00578_gb300 import raster as r
+
+    return r
+
+
+def tiny_scene(n=40, seed=50, w=48, h=40):
+    scene = synth.uniform_box_scene(n, seed=seed, half=1.0, log_scale_mu=-2.5, log_scale_sd=0.4)
+    cam = synth.look_at(w, h, 60.0, (0.4, -0.3, -4.0), (0.0, 0.0, 0.0))
+    return scene, cam
+
+
+def gpu_grads(raster, scene, cam, W, mode, tile=16, bg=(0.0, 0.0, 0.0)):
+    r = raster.Renderer("cuda:0")
+    ds = scene.to("cuda:0")
+    out = r.render(ds, cam, mode, tile, bg)
+    n = scene.n
+    grads = {k: torch.empty_like(getattr(ds, k)) for k in KEYS}
+    grads["means2d"] = torch.empty(2, n, device="cuda:0")
+    grads["score"] = torch.zeros(n, device="cuda:0")
+    work = torch.empty(raster.backward_work_bytes(n) // 4, device="cuda:0")
+    dL = torch.as_tensor(np.asarray(W, np.float32)).cuda().contiguous()
+    r.rast.gs_render_backward(ds, cam, raster.cfg_struct(tile, mode, bg), out.frame, dL, grads, work)
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy().astype(np.float64) for k, v in grads.items()}, out
+
+
+def rel_l2(a, b):
+    return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-30)
+
+
+@pytest.mark.parametrize("mode", [2, 0])
+@pytest.mark.parametrize("tile", [16, 8])
+def test_gradients_match_oracle(raster, mode, tile):
+    scene, cam = tiny_scene()
+    rng = np.random.default_rng(60)
+    W = rng.normal(size=(3, cam.height, cam.width))
+    bg = (0.2, 0.1, 0.3)
+    g, _ = gpu_grads(raster, scene, cam, W, mode, tile, bg)
+    ref, g2d = oracle.backward(scene, cam, W, tile, mode, bg)
+    for k in KEYS:
+        assert rel_l2(g[k], ref[k]) <= 1e-3, (k, rel_l2(g[k], ref[k]))
+    assert rel_l2(g["means2d"], g2d[0:2]) <= 1e-3
+    assert rel_l2(g["score"], g2d[9]) <= 1e-3
+    assert np.all(g["score"] >= 0)
+
+
+def test_gradients_match_oracle_box_16k(raster):
+    scene, cam = synth.small_box_workload()
+    rng = np.random.default_rng(61)
+    W = rng.normal(size=(3, cam.height, cam.width))
+    g, _ = gpu_grads(raster, scene, cam, W, 2)
+    ref, g2d = oracle.backward(scene, cam, W, 16, 2)
+    for k in KEYS:
+        assert rel_l2(g[k], ref[k]) <= 1e-3, (k, rel_l2(g[k], ref[k]))
+    assert rel_l2(g["score"], g2d[9]) <= 1e-3
+
+
+def test_finite_differences_of_gpu_forward(raster):
+    scene, cam = tiny_scene(seed=62)
+    rng = np.random.default_rng(63)
+    W = rng.normal(size=(3, cam.height, cam.width))
+    g, _ = gpu_grads(raster, scene, cam, W, 2)
+    r = raster.Renderer("cuda:0")
+
+    def L(sc):
+        img = r.render(sc.to("cuda:0"), cam, "accutile", 16).image.cpu().numpy().astype(np.float64)
+        return float((W * img).sum())
+
+    rms = {k: np.sqrt(np.mean(g[k] ** 2)) for k in KEYS}
+    contributing = np.nonzero(np.abs(g["means2d"]).sum(0) > 0)[0]
+    checked = 0
+    for trial in range(160):
+        key = KEYS[trial % 5]
+        i = int(rng.choice(contributing))
+        arr = getattr(scene, key)
+        idx = {"means": (int(rng.integers(3)), i), "scales": (int(rng.integers(3)), i),
+               "rotations": (int(rng.integers(4)), i), "opacities": (i,),
+               "sh": (int(rng.integers(16)), int(rng.integers(3)), i)}[key]
+        x0 = float(arr[idx])
+        h = max(abs(x0) * 1e-2, 1e-3)
+        fds = []
+        for step in (h, h / 2):
+            plus, minus = synth.Scene(*(getattr(scene, k).clone() for k in KEYS)), \
+                synth.Scene(*(getattr(scene, k).clone() for k in KEYS))
+            getattr(plus, key)[idx] = x0 + step
+            getattr(minus, key)[idx] = x0 - step
+            he = (float(getattr(plus, key)[idx]) - float(getattr(minus, key)[idx])) / 2
+            fds.append((L(plus) - L(minus)) / (2 * he))
+        if abs(fds[0] - fds[1]) > 2e-2 * max(abs(fds[1]), rms[key]):
+            continue  # crossed a threshold, clamp or stop decision
+        denom = max(abs(fds[1]), 1e-2 * rms[key])
+        assert abs(g[key][idx] - fds[1]) / denom <= 2e-2, (key, idx, g[key][idx], fds)
+        checked += 1
+    assert checked >= 64
+
+
+def test_autograd_function_and_score_accumulation(raster):
+    scene, cam = tiny_scene(seed=64)
+    rng = np.random.default_rng(65)
+    W = torch.as_tensor(rng.normal(size=(3, cam.height, cam.width)), dtype=torch.float32, device="cuda:0")
+    ds = scene.to("cuda:0")
+    params = [getattr(ds, k).clone().requires_grad_(True) for k in KEYS]
+    diff = raster.DiffRenderer("cuda:0")
+    diff.score = torch.zeros(scene.n, device="cuda:0")
+    for _ in range(2):
+        img = diff.render(*params, cam)
+        (img * W).sum().backward()
+    g, _ = gpu_grads(raster, scene, cam, W.cpu().numpy(), 2)
+    for k, p in zip(KEYS, params):
+        assert rel_l2(p.grad.cpu().numpy().astype(np.float64), 2 * g[k]) <= 1e-5, k
+    assert rel_l2(diff.score.cpu().numpy().astype(np.float64), 2 * g["score"]) <= 1e-5
+    # a re-render between forward and backward is detected
+    img = diff.render(*params, cam)
+    diff.render(*params, cam)
+    with pytest.raises(RuntimeError):
+        (img * W).sum().backward()
+
+
+def test_differentiable_1m_980x545_l1_dssim(raster):
+    """1M-Gaussian blob scene at 980x545, L1 + D-SSIM loss against a seeded
+    target (the same scene with jittered means and SH): GPU gradients against
+    the FP64 oracle given the same dL/dimage, on every Gaussian."""
+    from paper_2412_00578_gb300 import losses
+
+    scene = synth.blob_scene(1_000_000, seed=2)
+    cam = synth.pinhole(980, 545, 60.0, np.eye(3), np.array([0.0, 0.0, 25.0]))
+    gen = torch.Generator().manual_seed(3)
+    target_scene = synth.Scene(scene.means + 0.01 * torch.randn(scene.means.shape, generator=gen), scene.scales,
+                               scene.rotations, scene.opacities, scene.sh + 0.1 * torch.randn(scene.sh.shape, generator=gen))
+    r = raster.Renderer("cuda:0")
+    target = r.render(target_scene.to("cuda:0"), cam, "accutile", 16).image.clone()
+    ds = scene.to("cuda:0")
+    params = [getattr(ds, k).clone().requires_grad_(True) for k in KEYS]
+    diff = raster.DiffRenderer("cuda:0")
+    diff.score = torch.zeros(scene.n, device="cuda:0")
+    img = diff.render(*params, cam)
+    img.retain_grad()
+    loss = losses.gs_loss(img, target)
+    loss.backward()
+    dL = img.grad.detach().cpu().numpy().astype(np.float64)
+    ref, g2d = oracle.backward(scene, cam, dL, 16, 2)
+    for k, p in zip(KEYS, params):
+        e = rel_l2(p.grad.cpu().numpy().astype(np.float64), ref[k])
+        assert e <= 1e-3, (k, e)
+    assert rel_l2(diff.score.cpu().numpy().astype(np.float64), g2d[9]) <= 1e-3
+    print(f"1M diff render: loss {float(loss.detach()):.5f}, score nonzero {int((g2d[9] > 0).sum())}")
