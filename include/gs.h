@@ -230,6 +230,29 @@ int64_t gs_backward_work_bytes(int64_t n_capacity);
 gs_status gs_render_backward(gs_context* ctx, const gs_scene* scene, const gs_camera* cam, const gs_raster_cfg* cfg,
                              const gs_frame* frame, const float* dL_dimage, const gs_grads* grads);
 
+/* gs_intersect for callers that cannot allocate device memory (a plug-in
+ * whose host application owns all GPU allocations, a real-time loop that must
+ * not stall on an allocation, a program that forbids allocation after
+ * start-up).  The paper has no counterpart: this is a deployment variant of
+ * gs_intersect.  It does the same work and writes the same keys[0]/vals[0],
+ * but keeps its working memory (running sums of the counts and status words)
+ * in a fixed array built into the library instead of frame->scratch, which
+ * may be NULL and is never touched.
+ *   - Limit: frame->n_capacity <= 16,777,216 (GS_ERR_INVALID beyond, with a
+ *     message); the array takes about 131 KB on every device that loads the
+ *     library, until the process exits.
+ *   - num_keys (host) is required: the call synchronises the stream and
+ *     returns K there (GS_ERR_CAPACITY if K > key_capacity, nothing emitted).
+ *     The frame's own status words are not written, so the later stages
+ *     (gs_sort ...) need gs_intersect.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Allocates nothing; all calls on a device share the array and it keeps
+ *     the last call's contents (the call clears what must start at zero), so
+ *     calls whose GPU work overlaps (other streams or host threads) race. */
+gs_status gs_intersect_noalloc(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame,
+                               int64_t* num_keys);
+
 /* Synchronise the stream and read the frame's device status: the key total
  * K and the GS_FLAG_* bits (both host outputs, nullable).  Returns
  * GS_ERR_CAPACITY or GS_ERR_TIMEOUT if the corresponding flag is set. */

@@ -64,7 +64,7 @@ class GsFrameBytes(ctypes.Structure):
 
 EXPORTS = ["gs_create", "gs_destroy", "gs_set_stream", "gs_last_error", "gs_launch_count", "gs_frame_sizes",
            "gs_preprocess", "gs_intersect", "gs_sort", "gs_tile_ranges", "gs_render", "gs_render_stats",
-           "gs_forward", "gs_read_status", "gs_backward_work_bytes", "gs_render_backward"]
+           "gs_forward", "gs_read_status", "gs_backward_work_bytes", "gs_render_backward", "gs_intersect_noalloc"]
 
 _lib = None
 
@@ -98,6 +98,8 @@ def load(path=None) -> ctypes.CDLL:
     L.gs_render_stats.argtypes = [P, POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame),
                                   POINTER(ctypes.c_uint64), POINTER(ctypes.c_uint64), POINTER(ctypes.c_uint64)]
     L.gs_backward_work_bytes.argtypes = [c_int64]
+    L.gs_intersect_noalloc.argtypes = [P, POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame),
+                                       POINTER(c_int64)]
     L.gs_render_backward.argtypes = [P, POINTER(GsScene), POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame),
                                      P, POINTER(GsGrads)]
     for name in EXPORTS:
@@ -254,6 +256,15 @@ class Rasterizer:
         self._check(self.lib.gs_intersect(self.ctx, ctypes.byref(c), ctypes.byref(cfg), ctypes.byref(frame.struct),
                                           None), "gs_intersect")
         return None
+
+    def gs_intersect_noalloc(self, cam, cfg, frame_struct: GsFrame) -> int:
+        """gs_intersect without caller scratch (frame_struct.scratch may be None);
+        synchronises and returns the key total K."""
+        c = camera_struct(cam)
+        k = c_int64(0)
+        self._check(self.lib.gs_intersect_noalloc(self.ctx, ctypes.byref(c), ctypes.byref(cfg),
+                                                  ctypes.byref(frame_struct), ctypes.byref(k)), "gs_intersect_noalloc")
+        return int(k.value)
 
     def gs_sort(self, cam, cfg, frame: Frame):
         c = camera_struct(cam)
