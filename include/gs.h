@@ -52,6 +52,7 @@ typedef enum gs_mode {
 /* Device status word flags (gs_read_status). */
 #define GS_FLAG_CAPACITY 1u   /* keys did not fit: nothing was emitted            */
 #define GS_FLAG_TIMEOUT  2u   /* a sort look-back wait exceeded its bound         */
+#define GS_FLAG_BATCH    4u   /* batch cameras exceed the frame's tile or pixel capacity */
 
 /* Gaussian parameter set G_i = {mu, s, r, h, sigma} (Sec. 3.1), planar
  * structure of arrays, float32, device memory, read only.
@@ -85,11 +86,15 @@ typedef struct gs_camera {
     float campos[3];
 } gs_camera;
 
-/* Raster configuration: tile edge (8, 16 or 32 pixels), gs_mode, background. */
+/* Raster configuration: tile edge (8, 16 or 32 pixels), gs_mode, background,
+ * and the radix sort's digit width (0 = automatic: the fewest even number of
+ * 8-bit-or-narrower passes; 4..8 = at most that many bits per pass).  The
+ * digit width changes speed only, never the sorted result. */
 typedef struct gs_raster_cfg {
     int32_t tile;
     int32_t mode;
     float bg[3];
+    int32_t sort_digit_bits;
 } gs_raster_cfg;
 
 /* Per-frame buffers, all device memory owned by the caller, sized by
@@ -252,6 +257,62 @@ gs_status gs_render_backward(gs_context* ctx, const gs_scene* scene, const gs_ca
  *     calls whose GPU work overlaps (other streams or host threads) race. */
 gs_status gs_intersect_noalloc(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame,
                                int64_t* num_keys);
+
+/* ---------------------------------------------------------------- multi-view
+ * Many cameras of one scene in one batch: each stage is one launch over all
+ * cameras.  Tiles of all cameras share one global index space (camera c's
+ * tiles start at the sum of the earlier cameras' tile counts), so the keys of
+ * every camera go through one sort, one range pass and one blend launch.
+ * Grid sizes come from the frame's capacities and the per-camera layout is
+ * built on the device from a device array of cameras, so a captured CUDA
+ * graph of gs_forward_batch replays for new camera poses (same or smaller
+ * total tiles and pixels) after the caller rewrites that array.
+ * Buffers (device, caller-owned), for capacities n_capacity (Gaussian slots
+ * per camera), max_cams, tile_capacity (>= total tiles of one call),
+ * pixel_capacity (>= total pixels of one call), key_capacity:
+ *   proj [3][max_cams * n_capacity][4], counts [max_cams * n_capacity],
+ *   keys [2][key_capacity], vals [2][key_capacity] (value = index in the scene),
+ *   ranges [tile_capacity][2],
+ *   image [3 * pixel_capacity]: camera c's [3][H_c][W_c] image starts at
+ *   3 * P_c where P_c = sum of W*H over cameras before c; final_T and last
+ *   [pixel_capacity]: camera c's [H_c][W_c] plane starts at P_c. */
+#define GS_MAX_BATCH_CAMS 1024
+
+typedef struct gs_batch_frame {
+    int64_t n_capacity;
+    int64_t key_capacity;
+    int64_t tile_capacity;
+    int64_t pixel_capacity;
+    int32_t max_cams;
+    int32_t tile;
+    float* proj;
+    int32_t* counts;
+    uint64_t* keys;
+    uint32_t* vals;
+    uint32_t* ranges;
+    float* image;
+    float* final_T;
+    uint32_t* last;
+    void* scratch;
+} gs_batch_frame;
+
+/* Byte sizes of the gs_batch_frame buffers (fields as in gs_frame_bytes). */
+gs_status gs_batch_sizes(int64_t n_capacity, int32_t max_cams, int32_t tile, int64_t tile_capacity,
+                         int64_t pixel_capacity, int64_t key_capacity, gs_frame_bytes* out);
+
+/* The forward of Sec. 3.2 for num_cams cameras of one scene (cams: DEVICE
+ * array of num_cams gs_camera structs, read when the work runs).  Same
+ * per-camera results as gs_forward on each camera (same keys in the camera's
+ * tiles, same images, bit for bit).  No host synchronisation.  If the cameras
+ * exceed tile_capacity or pixel_capacity nothing is rendered and
+ * GS_FLAG_BATCH is set; if the keys exceed key_capacity, GS_FLAG_CAPACITY. */
+gs_status gs_forward_batch(gs_context* ctx, const gs_scene* scene, const gs_camera* cams, int32_t num_cams,
+                           const gs_raster_cfg* cfg, const gs_batch_frame* frame);
+
+/* Synchronise and read a batch frame's key total and GS_FLAG_* bits
+ * (host outputs, nullable); returns GS_ERR_CAPACITY / GS_ERR_TIMEOUT /
+ * GS_ERR_INVALID (for GS_FLAG_BATCH) when a flag is set. */
+gs_status gs_batch_status(gs_context* ctx, const gs_batch_frame* frame, int64_t* num_keys, uint32_t* flags);
 
 /* Synchronise the stream and read the frame's device status: the key total
  * K and the GS_FLAG_* bits (both host outputs, nullable).  Returns

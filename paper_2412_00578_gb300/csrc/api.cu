@@ -29,13 +29,9 @@ gs_status check_launch(gs_context* ctx, const char* what) {
 int64_t scan_blocks_for(int64_t n) { return (n + kScanBlock - 1) / kScanBlock; }
 
 namespace {
-
 constexpr int64_t kAlign = 256;
 int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
-
-struct ScratchLayout {
-    int64_t status, partials, hist, lookback, total;
-};
+}  // namespace
 
 ScratchLayout scratch_layout(int64_t ncap, int64_t kcap) {
     ScratchLayout L;
@@ -52,6 +48,8 @@ ScratchLayout scratch_layout(int64_t ncap, int64_t kcap) {
     return L;
 }
 
+namespace {
+
 bool valid_tile(int t) { return t == 8 || t == 16 || t == 32; }
 
 gs_status check_cam(gs_context* ctx, const gs_camera* cam, const gs_frame* f) {
@@ -67,6 +65,8 @@ gs_status check_cfg(gs_context* ctx, const gs_raster_cfg* cfg, const gs_frame* f
     if (cfg->tile != f->tile) return set_error(ctx, GS_ERR_INVALID, "cfg tile %d != frame tile %d", cfg->tile, f->tile);
     if (cfg->mode < GS_MODE_3SIGMA || cfg->mode > GS_MODE_ACCUTILE)
         return set_error(ctx, GS_ERR_INVALID, "mode %d is not a gs_mode", cfg->mode);
+    if (cfg->sort_digit_bits != 0 && (cfg->sort_digit_bits < 4 || cfg->sort_digit_bits > 8))
+        return set_error(ctx, GS_ERR_INVALID, "sort_digit_bits %d not in {0, 4..8}", cfg->sort_digit_bits);
     return GS_OK;
 }
 
@@ -224,7 +224,7 @@ gs_status gs_sort(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cf
     FrameView v;
     if (!make_view(ctx, frame, &v)) return GS_ERR_INVALID;
     if ((st = check_cam(ctx, cam, frame)) || (st = check_cfg(ctx, cfg, frame))) return st;
-    return launch_sort(ctx, v);
+    return launch_sort(ctx, v, cfg->sort_digit_bits);
 }
 
 gs_status gs_tile_ranges(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame) {

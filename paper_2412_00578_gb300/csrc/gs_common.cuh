@@ -20,8 +20,26 @@ constexpr int kMaxTile = 32;
 // ---------------------------------------------------------------- status words
 // scratch layout starts with these words (device):
 //   [0] key total K, low 32 bits   [1] K high bits   [2] GS_FLAG_* bits
+//   [3] multi-view set-up flags (GS_FLAG_BATCH), written by every batch set-up
 //   [4..9] three 64-bit counters of the instrumented blend (gs_render_stats)
 constexpr int kStatusWords = 16;
+
+// Camera constants as the kernels use them.
+struct CamK {
+    float fx, fy, cx, cy, limx, limy, near_z;
+    float V[12];
+    float campos[3];
+};
+
+// One camera of a multi-view batch (device table built by the batch set-up
+// kernel): constants, raster size, and where its tiles and pixels start in
+// the batch's global tile index space and packed image buffers.
+struct CamRec {
+    CamK k;
+    int width, height, gx, gy;
+    long long tile_offset;
+    long long pix_offset;
+};
 
 struct FrameView {
     int64_t ncap, kcap;
@@ -44,6 +62,11 @@ struct FrameView {
     uint32_t* sort_ticket;     // [kMaxPasses]
     uint32_t* sort_lookback;   // [2][sort_partitions][256] look-back words, see sort.cu
     int64_t sort_partitions;   // partitions the look-back table holds
+    // multi-view batches only (table == nullptr for a single camera)
+    const CamRec* table = nullptr;
+    int num_cams = 1;
+    int64_t cam_stride = 0;    // Gaussian slots per camera in proj/counts
+    int64_t pixel_capacity = 0;
 };
 
 // ---------------------------------------------------------------- scan / sort geometry
@@ -54,7 +77,7 @@ constexpr int kScanBlock = kScanThreads * kScanItems;
 constexpr int kSortThreads = 512;
 constexpr int kSortItems = 8;
 constexpr int kSortPartition = kSortThreads * kSortItems;  // keys per onesweep partition
-constexpr int kMaxPasses = 8;
+constexpr int kMaxPasses = 12;
 
 // ---------------------------------------------------------------- elementary functions
 // Natural logarithm: frexp range reduction to m in [sqrt(1/2), sqrt(2)),
@@ -137,8 +160,13 @@ namespace gs {
 gs_status set_error(gs_context* ctx, gs_status st, const char* fmt, ...);
 gs_status check_launch(gs_context* ctx, const char* what);
 bool make_view(gs_context* ctx, const gs_frame* f, FrameView* v);
-int sort_tile_bits(int tiles);
-void sort_plan(int tiles, int* passes, int* digit_bits);
+int sort_tile_bits(int64_t tiles);
+void sort_plan(int64_t tiles, int digit_override, int* passes, int* digit_bits);
+
+struct ScratchLayout {
+    int64_t status, partials, hist, lookback, total;
+};
+ScratchLayout scratch_layout(int64_t ncap, int64_t kcap);
 int64_t sort_partitions_for(int64_t kcap);
 int64_t scan_blocks_for(int64_t n);
 
@@ -146,7 +174,7 @@ int64_t scan_blocks_for(int64_t n);
 gs_status launch_preprocess(gs_context* ctx, const gs_scene* s, const gs_camera* cam, const gs_raster_cfg* cfg,
                             const FrameView& v);
 gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v);
-gs_status launch_sort(gs_context* ctx, const FrameView& v);
+gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override = 0);
 gs_status launch_ranges(gs_context* ctx, const FrameView& v);
 gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v,
                         unsigned long long* stats = nullptr);

@@ -103,6 +103,8 @@ struct EmitArgs {
     int64_t n;
     int mode;
     Grid grid;
+    const CamRec* table;  // multi-view (else nullptr)
+    int64_t cam_stride;   // Gaussian slots per camera
 };
 
 struct KeyWriter {
@@ -113,9 +115,10 @@ struct KeyWriter {
     uint32_t depth_bits;
     uint32_t id;
     int gx;
+    uint32_t tile0;  // first global tile of this camera (multi-view), else 0
     __device__ __forceinline__ void put(uint32_t tile) {
         if (pos < end) {  // the recount always equals the count; never write past it regardless
-            keys[pos] = ((uint64_t)tile << 32) | depth_bits;
+            keys[pos] = ((uint64_t)(tile0 + tile) << 32) | depth_bits;
             vals[pos] = id;
         }
         ++pos;
@@ -131,12 +134,15 @@ struct KeyWriter {
     }
 };
 
+template <bool kMulti>
 __global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
     __shared__ long long s_warp[32];
     if (A.status[2] & GS_FLAG_CAPACITY) return;  // keys do not fit: emit nothing
-    // The block's 1024 Gaussians are taken in 4 rounds of 256 consecutive
-    // ones (one per thread), so the 2D-state loads of a round are coalesced
-    // and neighbouring threads write neighbouring key ranges.
+    if (kMulti && A.status[3]) return;           // cameras do not fit the batch frame
+    // The block's 1024 slots are taken in 4 rounds of 256 consecutive ones
+    // (one per thread), so the 2D-state loads of a round are coalesced and
+    // neighbouring threads write neighbouring key ranges.  A slot is a
+    // Gaussian (single view) or a (camera, Gaussian) pair, camera-major.
     long long carry = A.partials[blockIdx.x];
     const int64_t block0 = (int64_t)blockIdx.x * kScanBlock;
 #pragma unroll 1
@@ -148,23 +154,33 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
         __syncthreads();  // s_warp is reused by the next round's scan
         carry += total;
         if (c == 0) continue;
+        Grid grid = A.grid;
+        uint32_t tile0 = 0, id = (uint32_t)i;
+        if (kMulti) {
+            const int64_t cam = i / A.cam_stride;
+            const CamRec& R = A.table[cam];
+            grid.gx = R.gx;
+            grid.gy = R.gy;
+            tile0 = (uint32_t)R.tile_offset;
+            id = (uint32_t)(i - cam * A.cam_stride);
+        }
         const float4 q0 = A.p0[i];
-        KeyWriter W{A.keys, A.vals, off, off + c, __float_as_uint(q0.w), (uint32_t)i, A.grid.gx};
+        KeyWriter W{A.keys, A.vals, off, off + c, __float_as_uint(q0.w), id, grid.gx, tile0};
         if (A.mode == GS_MODE_3SIGMA) {
             Rect R;
-            if (sigma3_rect(q0.x, q0.y, __float_as_int(A.p2[i].w), A.grid, R))
+            if (sigma3_rect(q0.x, q0.y, __float_as_int(A.p2[i].w), grid, R))
                 for (int ty = R.y0; ty <= R.y1; ++ty)
-                    for (int tx = R.x0; tx <= R.x1; ++tx) W.put((uint32_t)(ty * A.grid.gx + tx));
+                    for (int tx = R.x0; tx <= R.x1; ++tx) W.put((uint32_t)(ty * grid.gx + tx));
         } else {
             const float4 q1 = A.p1[i];
             const Ellipse E{q0.x, q0.y, q1.x, q1.y, q1.z, q1.w};
             Snug S;
-            if (snugbox(E, A.grid, S)) {
+            if (snugbox(E, grid, S)) {
                 if (A.mode == GS_MODE_SNUGBOX) {
                     for (int ty = S.R.y0; ty <= S.R.y1; ++ty)
-                        for (int tx = S.R.x0; tx <= S.R.x1; ++tx) W.put((uint32_t)(ty * A.grid.gx + tx));
+                        for (int tx = S.R.x0; tx <= S.R.x1; ++tx) W.put((uint32_t)(ty * grid.gx + tx));
                 } else {
-                    accutile_sweep(E, S, A.grid, W);
+                    accutile_sweep(E, S, grid, W);
                 }
             }
         }
@@ -175,7 +191,9 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
 
 gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v) {
     const int64_t nb = scan_blocks_for(v.ncap);
-    if (cudaMemsetAsync(v.status, 0, kStatusWords * sizeof(uint32_t), ctx->stream) != cudaSuccess)
+    // clear the key total and flags: words 0..2, and word 3 too for a single
+    // camera (a batch's set-up kernel has just written its word 3)
+    if (cudaMemsetAsync(v.status, 0, (v.table ? 3 : 4) * sizeof(uint32_t), ctx->stream) != cudaSuccess)
         return set_error(ctx, GS_ERR_CUDA, "intersect: cudaMemsetAsync(status) failed");
     if (nb > 0) {
         scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(v.counts, v.ncap, v.scan_partials);
@@ -196,7 +214,10 @@ gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const Fram
         A.n = v.ncap;
         A.mode = cfg->mode;
         A.grid = Grid{(float)v.tile, v.gx, v.gy};
-        emit_kernel<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(A);
+        A.table = v.table;
+        A.cam_stride = v.cam_stride;
+        if (v.table) emit_kernel<true><<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(A);
+        else emit_kernel<false><<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(A);
         ctx->launches += 1;
     }
     return check_launch(ctx, "intersect");

@@ -11,12 +11,6 @@
 namespace gs {
 namespace {
 
-struct CamK {
-    float fx, fy, cx, cy, limx, limy, near_z;
-    float V[12];
-    float campos[3];
-};
-
 struct PreArgs {
     const float* means;
     const float* scales;
@@ -33,6 +27,8 @@ struct PreArgs {
     float4* p1;
     float4* p2;
     int32_t* counts;
+    const CamRec* table;  // multi-view: per-camera constants (else nullptr)
+    int num_cams;
 };
 
 // Real SH normalisation constants, from their closed forms:
@@ -70,9 +66,9 @@ __device__ __forceinline__ void sh_basis16(float x, float y, float z, float Y[16
     Y[15] = ((-kC3a) * x) * (xx - 3.0f * yy);
 }
 
-__global__ void __launch_bounds__(256, 4) preprocess_kernel(const PreArgs A) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.ncap) return;
+// Gaussian i seen by camera C (grid g); writes slot o of the outputs.
+__device__ __forceinline__ void preprocess_one(const PreArgs& A, const CamK& C, const Grid& grid, int64_t i,
+                                               int64_t o) {
     int count = 0;
     if (i < A.n) {
         const int64_t n = A.n;
@@ -81,7 +77,6 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(const PreArgs A) {
         const float qw = __ldg(A.rots + i), qx = __ldg(A.rots + n + i), qy = __ldg(A.rots + 2 * n + i),
                     qz = __ldg(A.rots + 3 * n + i);
         const float sigma = __ldg(A.opac + i);
-        const CamK& C = A.cam;
         bool ok = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(s0) && isfinite(s1) && isfinite(s2) &&
                   isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) && isfinite(sigma);
         // view transform
@@ -161,7 +156,7 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(const PreArgs A) {
                     const float rad = ceilf(3.0f * sqrtf(l1));
                     const int radius = (rad >= 0.0f && rad < 1073741824.0f) ? (int)rad : (1 << 30);
                     const Ellipse E{u, v, a, b, c, t};
-                    count = tile_count(A.mode, E, radius, A.grid);
+                    count = tile_count(A.mode, E, radius, grid);
                     if (count > 0) {
                         // SH colour, read only for Gaussians that touch a tile
                         const float d0 = mx - C.campos[0], d1 = my - C.campos[1], d2 = mz - C.campos[2];
@@ -184,15 +179,32 @@ __global__ void __launch_bounds__(256, 4) preprocess_kernel(const PreArgs A) {
                             acc = acc + 0.5f;
                             rgb[ch] = acc < 0.0f ? 0.0f : acc;
                         }
-                        A.p0[i] = make_float4(u, v, sigma, pz);
-                        A.p1[i] = make_float4(a, b, c, t);
-                        A.p2[i] = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(radius));
+                        A.p0[o] = make_float4(u, v, sigma, pz);
+                        A.p1[o] = make_float4(a, b, c, t);
+                        A.p2[o] = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(radius));
                     }
                 }
             }
         }
     }
-    A.counts[i] = count;
+    A.counts[o] = count;
+}
+
+__global__ void __launch_bounds__(256, 4) preprocess_kernel(const PreArgs A) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.ncap) return;
+    preprocess_one(A, A.cam, A.grid, i, i);
+}
+
+// Multi-view: block b handles Gaussian chunk b / V for camera b % V, so the
+// cameras of one chunk run back to back and re-read its parameters from L2.
+__global__ void __launch_bounds__(256, 4) preprocess_multiview_kernel(const PreArgs A) {
+    const int cam = (int)(blockIdx.x % (unsigned)A.num_cams);
+    const int64_t i = (int64_t)(blockIdx.x / (unsigned)A.num_cams) * blockDim.x + threadIdx.x;
+    if (i >= A.ncap) return;
+    const CamRec& R = A.table[cam];
+    const Grid g{A.grid.T, R.gx, R.gy};
+    preprocess_one(A, R.k, g, i, (int64_t)cam * A.ncap + i);
 }
 
 }  // namespace
@@ -210,21 +222,33 @@ gs_status launch_preprocess(gs_context* ctx, const gs_scene* s, const gs_camera*
     A.sh_coeffs = (s->sh_degree + 1) * (s->sh_degree + 1);
     A.mode = cfg->mode;
     A.grid = Grid{(float)v.tile, v.gx, v.gy};
-    A.cam.fx = cam->fx;
-    A.cam.fy = cam->fy;
-    A.cam.cx = cam->cx;
-    A.cam.cy = cam->cy;
-    A.cam.limx = 1.3f * cam->tan_fovx;
-    A.cam.limy = 1.3f * cam->tan_fovy;
-    A.cam.near_z = cam->near_z;
-    for (int k = 0; k < 12; ++k) A.cam.V[k] = cam->viewmat[k];
-    for (int k = 0; k < 3; ++k) A.cam.campos[k] = cam->campos[k];
+    if (cam) {  // single camera: constants travel as kernel parameters
+        A.cam.fx = cam->fx;
+        A.cam.fy = cam->fy;
+        A.cam.cx = cam->cx;
+        A.cam.cy = cam->cy;
+        A.cam.limx = 1.3f * cam->tan_fovx;
+        A.cam.limy = 1.3f * cam->tan_fovy;
+        A.cam.near_z = cam->near_z;
+        for (int k = 0; k < 12; ++k) A.cam.V[k] = cam->viewmat[k];
+        for (int k = 0; k < 3; ++k) A.cam.campos[k] = cam->campos[k];
+    }
     A.p0 = v.p0;
     A.p1 = v.p1;
     A.p2 = v.p2;
     A.counts = v.counts;
-    if (v.ncap == 0) return GS_OK;
+    A.table = v.table;
+    A.num_cams = v.num_cams;
     const int threads = 256;
+    if (v.table) {
+        A.ncap = v.cam_stride;
+        if (A.ncap == 0 || v.num_cams == 0) return GS_OK;
+        const int64_t blocks = (A.ncap + threads - 1) / threads * v.num_cams;
+        preprocess_multiview_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(A);
+        ctx->launches += 1;
+        return check_launch(ctx, "preprocess_multiview");
+    }
+    if (v.ncap == 0) return GS_OK;
     const int64_t blocks = (v.ncap + threads - 1) / threads;
     preprocess_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(A);
     ctx->launches += 1;

@@ -23,8 +23,9 @@
 namespace gs {
 namespace {
 
+// Keys present in the buffer (see sort.cu): none when the emit was skipped.
 __device__ __forceinline__ uint32_t frame_keys_r(const uint32_t* status) {
-    return (status[2] & GS_FLAG_CAPACITY) ? 0u : status[0];
+    return ((status[2] & GS_FLAG_CAPACITY) || status[3]) ? 0u : status[0];
 }
 
 __global__ void __launch_bounds__(256) ranges_kernel(const uint64_t* __restrict__ keys,
@@ -57,9 +58,25 @@ struct BlendArgs {
     int width, height, gx;
     float bg0, bg1, bg2;
     unsigned long long* stats;  // [3]: defined, contributing, executed pair counts (stats variant)
+    const CamRec* table;        // multi-view (else nullptr)
+    int num_cams;
+    int64_t cam_stride;
+    int64_t pixel_capacity;
 };
 
-template <int T, bool kStats>
+// Camera owning global tile g of a multi-view batch: the last camera whose
+// first tile is <= g (tile offsets ascend with the camera index).
+__device__ __forceinline__ int camera_of_tile(const CamRec* table, int num_cams, long long g) {
+    int lo = 0, hi = num_cams - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (table[mid].tile_offset <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int T, bool kStats, bool kMulti>
 __global__ void __launch_bounds__(T* T, T == 32 ? 1 : 2) blend_kernel(const BlendArgs A) {
     constexpr int NT = T * T;
     constexpr int NB = NT < 256 ? NT : 256;  // Gaussians per shared-memory batch
@@ -68,13 +85,36 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : 2) blend_kernel(const Blen
     __shared__ float4 s_g1[NB];  // c, t, opacity, -
     __shared__ float4 s_g2[NB];  // r, g, b, -
     __shared__ uint32_t s_mask[NB];
-    const int tile = blockIdx.x;
-    const int tx = tile % A.gx, ty = tile / A.gx;
+    const int tile = blockIdx.x;  // global tile index
+    int gx = A.gx, width = A.width, height = A.height, local = tile;
+    float* image = A.image;
+    float* final_T = A.final_T;
+    uint32_t* last_out = A.last;
+    const float4* p0 = A.p0;
+    const float4* p1 = A.p1;
+    const float4* p2 = A.p2;
+    if (kMulti) {
+        const int cam = camera_of_tile(A.table, A.num_cams, tile);
+        const CamRec& R = A.table[cam];
+        if ((long long)tile >= R.tile_offset + (long long)R.gx * R.gy) return;  // beyond the last camera
+        if (R.pix_offset + (long long)R.width * R.height > A.pixel_capacity) return;
+        gx = R.gx;
+        width = R.width;
+        height = R.height;
+        local = (int)(tile - R.tile_offset);
+        image += 3 * R.pix_offset;
+        final_T += R.pix_offset;
+        last_out += R.pix_offset;
+        p0 += (int64_t)cam * A.cam_stride;
+        p1 += (int64_t)cam * A.cam_stride;
+        p2 += (int64_t)cam * A.cam_stride;
+    }
+    const int tx = local % gx, ty = local / gx;
     const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
     const uint32_t my_bit = 1u << warp;
     const int px = tx * T + (warp % NSX) * kSubW + (lane & (kSubW - 1));
     const int py = ty * T + (warp / NSX) * kSubH + (lane >> 3);
-    const bool inside = px < A.width && py < A.height;
+    const bool inside = px < width && py < height;
     const float pxf = (float)px, pyf = (float)py;
     const float ox = (float)(tx * T), oy = (float)(ty * T);
     const uint2 rg = A.ranges[tile];
@@ -88,11 +128,11 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : 2) blend_kernel(const Blen
         const int j = b0 + (int)threadIdx.x;
         if ((int)threadIdx.x < NB && j < n) {
             const uint32_t id = A.vals[rg.x + j];
-            const float4 q0 = A.p0[id];
-            const float4 q1 = A.p1[id];
+            const float4 q0 = p0[id];
+            const float4 q1 = p1[id];
             s_g0[threadIdx.x] = make_float4(q0.x, q0.y, q1.x, q1.y + q1.y);
             s_g1[threadIdx.x] = make_float4(q1.z, q1.w, q0.z, 0.0f);
-            s_g2[threadIdx.x] = A.p2[id];
+            s_g2[threadIdx.x] = p2[id];
             s_mask[threadIdx.x] = subtile_mask<T>(q0.x, q0.y, q1.x, q1.y, q1.z, q1.w, ox, oy);
         }
         __syncthreads();
@@ -133,13 +173,13 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : 2) blend_kernel(const Blen
         }
     }
     if (inside) {
-        const size_t HW = (size_t)A.width * A.height;
-        const size_t o = (size_t)py * A.width + px;
-        A.image[o] = fmaf(Tr, A.bg0, C0);
-        A.image[HW + o] = fmaf(Tr, A.bg1, C1);
-        A.image[2 * HW + o] = fmaf(Tr, A.bg2, C2);
-        A.final_T[o] = Tr;
-        A.last[o] = last;
+        const size_t HW = (size_t)width * height;
+        const size_t o = (size_t)py * width + px;
+        image[o] = fmaf(Tr, A.bg0, C0);
+        image[HW + o] = fmaf(Tr, A.bg1, C1);
+        image[2 * HW + o] = fmaf(Tr, A.bg2, C2);
+        final_T[o] = Tr;
+        last_out[o] = last;
     }
     if (kStats) {
         // pairs the tile-list definition evaluates: every entry up to the stop
@@ -185,23 +225,27 @@ gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameVi
     A.bg1 = cfg->bg[1];
     A.bg2 = cfg->bg[2];
     A.stats = stats;
+    A.table = v.table;
+    A.num_cams = v.num_cams;
+    A.cam_stride = v.cam_stride;
+    A.pixel_capacity = v.pixel_capacity;
     const unsigned tiles = (unsigned)(v.gx * v.gy);
     if (tiles == 0) return GS_OK;
-    if (stats) {
-        switch (v.tile) {
-            case 8: blend_kernel<8, true><<<tiles, 64, 0, ctx->stream>>>(A); break;
-            case 16: blend_kernel<16, true><<<tiles, 256, 0, ctx->stream>>>(A); break;
-            case 32: blend_kernel<32, true><<<tiles, 1024, 0, ctx->stream>>>(A); break;
-            default: return set_error(ctx, GS_ERR_INVALID, "render: tile %d not supported", v.tile);
-        }
-    } else {
-        switch (v.tile) {
-            case 8: blend_kernel<8, false><<<tiles, 64, 0, ctx->stream>>>(A); break;
-            case 16: blend_kernel<16, false><<<tiles, 256, 0, ctx->stream>>>(A); break;
-            case 32: blend_kernel<32, false><<<tiles, 1024, 0, ctx->stream>>>(A); break;
-            default: return set_error(ctx, GS_ERR_INVALID, "render: tile %d not supported", v.tile);
-        }
+#define GS_BLEND_LAUNCH(T_, S_, M_) blend_kernel<T_, S_, M_><<<tiles, T_ * T_, 0, ctx->stream>>>(A)
+#define GS_BLEND_TILES(S_, M_)                                                             \
+    switch (v.tile) {                                                                      \
+        case 8: GS_BLEND_LAUNCH(8, S_, M_); break;                                         \
+        case 16: GS_BLEND_LAUNCH(16, S_, M_); break;                                       \
+        case 32: GS_BLEND_LAUNCH(32, S_, M_); break;                                       \
+        default: return set_error(ctx, GS_ERR_INVALID, "render: tile %d not supported", v.tile); \
     }
+    if (v.table) {
+        if (stats) { GS_BLEND_TILES(true, true) } else { GS_BLEND_TILES(false, true) }
+    } else {
+        if (stats) { GS_BLEND_TILES(true, false) } else { GS_BLEND_TILES(false, false) }
+    }
+#undef GS_BLEND_TILES
+#undef GS_BLEND_LAUNCH
     ctx->launches += 1;
     return check_launch(ctx, "render");
 }

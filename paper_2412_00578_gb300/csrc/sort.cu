@@ -32,8 +32,10 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr uint32_t kNoDigit = 0xffffffffu;
 constexpr int kLookWindow = 8;  // predecessors inspected per look-back step
 
+// Keys present in the buffer: none when the emit was skipped (keys over
+// capacity, or batch cameras over the frame's tile/pixel capacity).
 __device__ __forceinline__ uint32_t frame_keys(const uint32_t* status) {
-    return (status[2] & GS_FLAG_CAPACITY) ? 0u : status[0];
+    return ((status[2] & GS_FLAG_CAPACITY) || status[3]) ? 0u : status[0];
 }
 
 struct HistArgs {
@@ -242,24 +244,29 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
 
 }  // namespace
 
-int sort_tile_bits(int tiles) {
+int sort_tile_bits(int64_t tiles) {
     int b = 0;
-    while ((1ll << b) < (long long)tiles) ++b;
+    while ((int64_t(1) << b) < tiles) ++b;
     return b;
 }
 
-void sort_plan(int tiles, int* passes, int* digit_bits) {
+// Even number of passes (the result returns to buffer 0) with at most 8 bits
+// per digit, or at most `digit_override` bits when it is 4..8.
+void sort_plan(int64_t tiles, int digit_override, int* passes, int* digit_bits) {
     const int bits = 32 + sort_tile_bits(tiles);
-    const int p = 2 * ((bits + 15) / 16);
+    const int dmax = (digit_override >= 4 && digit_override <= 8) ? digit_override : 8;
+    int p = (bits + dmax - 1) / dmax;
+    p += p & 1;
+    if (p > kMaxPasses) p = kMaxPasses;
     *passes = p;
     *digit_bits = (bits + p - 1) / p;
 }
 
 int64_t sort_partitions_for(int64_t kcap) { return (kcap + kSortPartition - 1) / kSortPartition; }
 
-gs_status launch_sort(gs_context* ctx, const FrameView& v) {
+gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override) {
     int passes, dbits;
-    sort_plan(v.gx * v.gy, &passes, &dbits);
+    sort_plan((int64_t)v.gx * v.gy, digit_override, &passes, &dbits);
     static bool attr_done[64] = {false};
     if (!attr_done[ctx->device & 63]) {
         if (cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -42,7 +42,7 @@ class GsCamera(ctypes.Structure):
 
 
 class GsRasterCfg(ctypes.Structure):
-    _fields_ = [("tile", c_int32), ("mode", c_int32), ("bg", c_float * 3)]
+    _fields_ = [("tile", c_int32), ("mode", c_int32), ("bg", c_float * 3), ("sort_digit_bits", c_int32)]
 
 
 class GsFrame(ctypes.Structure):
@@ -50,6 +50,13 @@ class GsFrame(ctypes.Structure):
                 ("tile", c_int32), ("proj", c_void_p), ("counts", c_void_p), ("keys", c_void_p),
                 ("vals", c_void_p), ("ranges", c_void_p), ("image", c_void_p), ("final_T", c_void_p),
                 ("last", c_void_p), ("scratch", c_void_p)]
+
+
+class GsBatchFrame(ctypes.Structure):
+    _fields_ = [("n_capacity", c_int64), ("key_capacity", c_int64), ("tile_capacity", c_int64),
+                ("pixel_capacity", c_int64), ("max_cams", c_int32), ("tile", c_int32), ("proj", c_void_p),
+                ("counts", c_void_p), ("keys", c_void_p), ("vals", c_void_p), ("ranges", c_void_p),
+                ("image", c_void_p), ("final_T", c_void_p), ("last", c_void_p), ("scratch", c_void_p)]
 
 
 class GsGrads(ctypes.Structure):
@@ -64,7 +71,8 @@ class GsFrameBytes(ctypes.Structure):
 
 EXPORTS = ["gs_create", "gs_destroy", "gs_set_stream", "gs_last_error", "gs_launch_count", "gs_frame_sizes",
            "gs_preprocess", "gs_intersect", "gs_sort", "gs_tile_ranges", "gs_render", "gs_render_stats",
-           "gs_forward", "gs_read_status", "gs_backward_work_bytes", "gs_render_backward", "gs_intersect_noalloc"]
+           "gs_forward", "gs_read_status", "gs_backward_work_bytes", "gs_render_backward", "gs_intersect_noalloc",
+           "gs_batch_sizes", "gs_forward_batch", "gs_batch_status"]
 
 _lib = None
 
@@ -98,6 +106,9 @@ def load(path=None) -> ctypes.CDLL:
     L.gs_render_stats.argtypes = [P, POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame),
                                   POINTER(ctypes.c_uint64), POINTER(ctypes.c_uint64), POINTER(ctypes.c_uint64)]
     L.gs_backward_work_bytes.argtypes = [c_int64]
+    L.gs_batch_sizes.argtypes = [c_int64, c_int32, c_int32, c_int64, c_int64, c_int64, POINTER(GsFrameBytes)]
+    L.gs_forward_batch.argtypes = [P, POINTER(GsScene), P, c_int32, POINTER(GsRasterCfg), POINTER(GsBatchFrame)]
+    L.gs_batch_status.argtypes = [P, POINTER(GsBatchFrame), POINTER(c_int64), POINTER(c_uint32)]
     L.gs_intersect_noalloc.argtypes = [P, POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame),
                                        POINTER(c_int64)]
     L.gs_render_backward.argtypes = [P, POINTER(GsScene), POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame),
@@ -139,11 +150,12 @@ def scene_struct(scene) -> GsScene:
     return s
 
 
-def cfg_struct(tile: int, mode, bg=(0.0, 0.0, 0.0)) -> GsRasterCfg:
+def cfg_struct(tile: int, mode, bg=(0.0, 0.0, 0.0), sort_digit_bits: int = 0) -> GsRasterCfg:
     c = GsRasterCfg()
     c.tile = int(tile)
     c.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     c.bg[:] = [float(x) for x in bg]
+    c.sort_digit_bits = int(sort_digit_bits)
     return c
 
 
@@ -311,12 +323,27 @@ class Rasterizer:
         self._check(self.lib.gs_forward(self.ctx, ctypes.byref(s), ctypes.byref(c), ctypes.byref(cfg),
                                         ctypes.byref(frame.struct)), "gs_forward")
 
+    def gs_forward_batch(self, scene, cams_dev: torch.Tensor, num_cams: int, cfg, frame: "BatchFrame"):
+        """cams_dev: device tensor holding num_cams packed gs_camera structs."""
+        s = scene_struct(scene)
+        self._check(self.lib.gs_forward_batch(self.ctx, ctypes.byref(s), c_void_p(cams_dev.data_ptr()),
+                                              int(num_cams), ctypes.byref(cfg), ctypes.byref(frame.struct)),
+                    "gs_forward_batch")
+
+    def gs_batch_status(self, frame: "BatchFrame", raise_on_error: bool = True):
+        k = c_int64(0)
+        fl = c_uint32(0)
+        st = self.lib.gs_batch_status(self.ctx, ctypes.byref(frame.struct), ctypes.byref(k), ctypes.byref(fl))
+        if st != 0 and (raise_on_error or st not in (1, 3, 5) or not fl.value):
+            self._check(st, "gs_batch_status")  # CUDA errors always raise
+        return int(k.value), int(fl.value)
+
     def gs_read_status(self, frame: Frame, raise_on_error: bool = True):
         k = c_int64(0)
         fl = c_uint32(0)
         st = self.lib.gs_read_status(self.ctx, ctypes.byref(frame.struct), ctypes.byref(k), ctypes.byref(fl))
-        if raise_on_error and st not in (0,):
-            self._check(st, "gs_read_status")
+        if st != 0 and (raise_on_error or st not in (3, 5) or not fl.value):
+            self._check(st, "gs_read_status")  # CUDA errors always raise
         return int(k.value), int(fl.value)
 
 
@@ -447,3 +474,154 @@ class DiffRenderer:
     def render(self, means, scales, rotations, opacities, sh, cam, sh_degree=3):
         return _RenderFn.apply(means, scales, rotations, opacities, sh, self, cam, self.mode, self.tile, self.bg,
                                sh_degree)
+
+
+# ---------------------------------------------------------------- multi-view
+FLAG_BATCH = 4
+CAMERA_BYTES = ctypes.sizeof(GsCamera)
+
+
+def pack_cameras(cams) -> torch.Tensor:
+    """Packed gs_camera structs as a uint8 CPU tensor (pinned) of len(cams) * CAMERA_BYTES."""
+    arr = (GsCamera * len(cams))(*[camera_struct(c) for c in cams])
+    host = torch.empty(len(cams) * CAMERA_BYTES, dtype=torch.uint8).pin_memory()
+    ctypes.memmove(host.data_ptr(), ctypes.addressof(arr), len(cams) * CAMERA_BYTES)
+    return host
+
+
+def batch_layout(cams, tile):
+    """Per-camera (tile offset, pixel offset) and totals, in camera order."""
+    toff, poff, t, p = [], [], 0, 0
+    for c in cams:
+        toff.append(t)
+        poff.append(p)
+        t += ((c.width + tile - 1) // tile) * ((c.height + tile - 1) // tile)
+        p += c.width * c.height
+    return toff, poff, t, p
+
+
+class BatchFrame:
+    """Caller-owned buffers of a multi-view batch (gs_batch_frame)."""
+
+    def __init__(self, n, max_cams, tile, tile_capacity, pixel_capacity, key_capacity, device=None):
+        device = torch.device(device or "cuda")
+        sz = GsFrameBytes()
+        st = load().gs_batch_sizes(int(n), int(max_cams), int(tile), int(tile_capacity), int(pixel_capacity),
+                                   int(key_capacity), ctypes.byref(sz))
+        if st != 0:
+            raise GsError(st, "gs_batch_sizes")
+        self.n, self.max_cams, self.tile = n, max_cams, tile
+        self.tile_capacity, self.pixel_capacity, self.key_capacity = tile_capacity, pixel_capacity, key_capacity
+        e = lambda nbytes, dt, es: torch.empty(max(nbytes // es, 1), dtype=dt, device=device)
+        self.proj = e(sz.proj, torch.float32, 4)
+        self.counts = e(sz.counts, torch.int32, 4)
+        self.keys = e(sz.keys, torch.int64, 8)
+        self.vals = e(sz.vals, torch.int32, 4)
+        self.ranges = e(sz.ranges, torch.int32, 4)
+        self.image = e(sz.image, torch.float32, 4)
+        self.final_T = e(sz.final_T, torch.float32, 4)
+        self.last = e(sz.last, torch.int32, 4)
+        self.scratch = e(sz.scratch, torch.uint8, 1)
+        self.cams_dev = torch.empty(max_cams * CAMERA_BYTES, dtype=torch.uint8, device=device)
+        f = GsBatchFrame()
+        f.n_capacity, f.key_capacity = n, key_capacity
+        f.tile_capacity, f.pixel_capacity = tile_capacity, pixel_capacity
+        f.max_cams, f.tile = max_cams, tile
+        for k in ("proj", "counts", "keys", "vals", "ranges", "image", "final_T", "last", "scratch"):
+            setattr(f, k, getattr(self, k).data_ptr())
+        self.struct = f
+
+    def images(self, cams):
+        """Views (3, H, W) of each camera's image in the packed buffer."""
+        _, poff, _, _ = batch_layout(cams, self.tile)
+        return [self.image[3 * p: 3 * p + 3 * c.width * c.height].view(3, c.height, c.width)
+                for c, p in zip(cams, poff)]
+
+    def nbytes(self) -> int:
+        return sum(t.numel() * t.element_size() for t in (self.proj, self.counts, self.keys, self.vals, self.ranges,
+                                                          self.image, self.final_T, self.last, self.scratch))
+
+
+class BatchRenderer:
+    """Renders many cameras of one scene per call (gs_forward_batch), growing
+    capacities on demand; ``capture``/``replay`` run the batch as a CUDA graph
+    whose camera poses are rewritten before each replay."""
+
+    def __init__(self, device=None, tile=16, mode="accutile", bg=(0.0, 0.0, 0.0), sort_digit_bits=0,
+                 headroom=1.25):
+        self.rast = Rasterizer(device)
+        self.device = self.rast.device
+        self.tile, self.mode, self.bg = tile, mode, bg
+        self.sort_digit_bits = sort_digit_bits
+        self.headroom = headroom
+        self.frame = None
+        self.graph = None
+
+    def cfg(self):
+        return cfg_struct(self.tile, self.mode, self.bg, self.sort_digit_bits)
+
+    def ensure(self, n, cams, min_keys=0):
+        _, _, T, P = batch_layout(cams, self.tile)
+        f = self.frame
+        if (f is None or f.n < n or f.max_cams < len(cams) or f.tile_capacity < T or f.pixel_capacity < P
+                or f.key_capacity < min_keys or f.tile != self.tile):
+            keys = max(int(min_keys), 1 << 20, f.key_capacity if f is not None else 0)
+            self.frame = BatchFrame(n, max(len(cams), f.max_cams if f else 0), self.tile,
+                                    max(T, f.tile_capacity if f else 0), max(P, f.pixel_capacity if f else 0),
+                                    min(keys, MAX_KEYS), self.device)
+            self.graph = None
+        return self.frame
+
+    def _launch(self, scene, cams):
+        f = self.frame
+        host = pack_cameras(cams)
+        f.cams_dev[: host.numel()].copy_(host, non_blocking=True)
+        self.rast.gs_forward_batch(scene, f.cams_dev, len(cams), self.cfg(), f)
+
+    def render(self, scene, cams):
+        """Returns the list of (3, H, W) images (views into the frame) and K."""
+        n = int(scene.means.shape[1])
+        self.ensure(n, cams)
+        self._launch(scene, cams)
+        K, flags = self.rast.gs_batch_status(self.frame, raise_on_error=False)
+        if flags & FLAG_CAPACITY:
+            self.ensure(n, cams, min_keys=int(K * self.headroom) + 1)
+            self._launch(scene, cams)
+            K, flags = self.rast.gs_batch_status(self.frame, raise_on_error=False)
+        if flags:
+            self.rast.gs_batch_status(self.frame, raise_on_error=True)
+        return self.frame.images(cams), K
+
+    def capture(self, scene, cams):
+        """Capture one batch as a CUDA graph (after a sizing render)."""
+        self.render(scene, cams)
+        f = self.frame
+        self._graph_scene = scene
+        self._graph_ncams = len(cams)
+        stream = torch.cuda.Stream(self.device)
+        stream.wait_stream(torch.cuda.current_stream(self.device))
+        g = torch.cuda.CUDAGraph()
+        old = self.rast.stream
+        with torch.cuda.stream(stream):
+            self.rast.set_stream(stream)
+            self.rast.gs_forward_batch(scene, f.cams_dev, len(cams), self.cfg(), f)  # warm on the side stream
+            stream.synchronize()
+            with torch.cuda.graph(g, stream=stream):
+                self.rast.gs_forward_batch(scene, f.cams_dev, len(cams), self.cfg(), f)
+        self.rast.set_stream(old)
+        torch.cuda.current_stream(self.device).wait_stream(stream)
+        self.graph = g
+        return g
+
+    def replay(self, cams=None):
+        """Replay the captured batch, optionally with new poses (same or fewer
+        tiles and pixels in total, same camera count)."""
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        f = self.frame
+        if cams is not None:
+            if len(cams) != self._graph_ncams:
+                raise ValueError("a replay keeps the captured camera count")
+            host = pack_cameras(cams)
+            f.cams_dev[: host.numel()].copy_(host, non_blocking=True)
+        self.graph.replay()
