@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--no-multiview", action="store_true")
     p.add_argument("--mv-cams", type=int, default=64)
     p.add_argument("--mv-n", type=int, default=1_500_000)
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-duration", type=float, default=1.5, help="seconds of arrivals per rate")
+    p.add_argument("--serve-rates", default="200,500,1000,2000")
     return p.parse_args()
 
 
@@ -397,6 +400,11 @@ def run_ours(args):
     if not args.no_multiview:
         multiview = run_multiview(args, dev, max_over_ranks, barrier)
 
+    # --- serving: resident scenes, Poisson arrivals, continuous batching
+    served = None
+    if not args.no_serve and rank == 0:
+        served = run_serving(args, dev, scene)
+
     if rank == 0:
         fps = world * 1e3 / ms_acc
         emit({"metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -409,7 +417,7 @@ def run_ours(args):
               "speedup_vs_3sigma": (per_mode["3sigma"]["ms_per_frame"] / ms_acc) if "3sigma" in per_mode else None,
               "stages_ms": stages, "stage_roofline": stage_frac,
               "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
-              "cpu_baseline": cpu, "multiview": multiview})
+              "cpu_baseline": cpu, "multiview": multiview, "served": served})
     if world > 1:
         dist.destroy_process_group()
 
@@ -458,6 +466,35 @@ def run_multiview(args, dev, max_over_ranks, barrier):
             "ms_per_batch_graph": ms_batch, "views_per_s": len(cams) * 1e3 / ms_batch,
             "ms_64_views_one_by_one": ms_seq, "speedup_vs_one_by_one": ms_seq / ms_batch,
             "keys": K, "status_flags": flags, "frame_gb": br.frame.nbytes() / 1e9}
+
+
+def run_serving(args, dev, scene_3m):
+    import torch
+
+    from paper_2412_00578_gb300 import serve, synth
+
+    scenes = {"300k": synth.blob_scene(300_000, seed=11).to(dev), "600k": synth.blob_scene(600_000, seed=12).to(dev),
+              "1.5M": synth.blob_scene(1_500_000, seed=13).to(dev), "3M": scene_3m}
+    res = synth.RESOLUTIONS
+
+    def cam_fn(gen):
+        w, h = res[int(torch.randint(len(res), (1,), generator=gen))]
+        return synth.orbit_camera(gen, w, h)
+
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(0.5 * free)
+    ex = serve.GpuExecutor(scenes, dev, slots=3)
+    warm = serve.poisson_requests(500.0, 0.05, list(scenes), cam_fn, seed=99)  # sizes the slot frames
+    serve.serve(warm, serve.Scheduler({k: v.n for k, v in scenes.items()}, max_batch=16, memory_budget=budget), ex)
+    out = {"scenes": {k: v.n for k, v in scenes.items()}, "slots": 3, "max_batch": 16,
+           "memory_budget_gb": budget / 1e9, "arrivals_s": args.serve_duration, "rates": {}}
+    for rate in [float(x) for x in args.serve_rates.split(",")]:
+        reqs = serve.poisson_requests(rate, args.serve_duration, list(scenes), cam_fn, seed=7)
+        sch = serve.Scheduler({k: v.n for k, v in scenes.items()}, max_batch=16, memory_budget=budget)
+        _, st = serve.serve(reqs, sch, ex)
+        out["rates"][str(int(rate))] = {k: st[k] for k in ("requests", "p50_ms", "p99_ms", "frames_per_s",
+                                                            "mean_batch", "max_inflight_batches", "span_s")}
+    return out
 
 
 def raster_sort_passes(width, height, tile):
