@@ -141,11 +141,52 @@ def peaks():
         return {"hbm_gbs": 6800.0, "src": "fallback", "sm_max_mhz": 2070.0}
 
 
+def blend_traffic(keys):
+    """DRAM bytes of one blend launch, from the ncu counters in
+    profiles/dram_traffic.json scaled per key, or None if the blend's sources
+    changed since those counters were taken."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            rec = json.load(f)["blend_kernel"]
+        h = hashlib.sha256()
+        for p in rec["sources"]:
+            with open(os.path.join(ROOT, p), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != rec["source_sha256"]:
+            return None
+        return rec["bytes_per_key"] * keys
+    except Exception:
+        return None
+
+
 def workload(args):
     from paper_2412_00578_gb300 import synth
 
     scene, cam = synth.outdoor_workload(n=args.n, width=args.width, height=args.height)
     return scene, cam
+
+
+def make_max_reduce(dist, device):
+    """max over ranks of a float (identity without torch.distributed)."""
+    import torch
+
+    def red(x: float) -> float:
+        if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+            return x
+        t = torch.tensor([x], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    return red
+
+
+def replica_rate(frames_per_rank: int, elapsed_ms_local: float, world: int, max_reduce):
+    """Whole-job frames/s of N replicas: all ranks' frames over the slowest
+    rank's elapsed time.  Returns (frames/s, ms per frame of one replica)."""
+    ms = max_reduce(elapsed_ms_local)
+    return world * frames_per_rank * 1e3 / ms, ms / frames_per_rank
 
 
 def emit(obj):
@@ -225,12 +266,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = make_max_reduce(dist if world > 1 else None, dev)
 
     modes = [m for m in args.modes.split(",") if m]
     assert modes and modes[0] == "accutile", "the headline mode is accutile"
@@ -259,7 +295,7 @@ def run_ours(args):
         barrier()
         clocks = sampler.stop() if sampler else None
         launches = rast.launch_count() - l0
-        ms = max_over_ranks(e0.elapsed_time(e1)) / steps
+        _, ms = replica_rate(steps, e0.elapsed_time(e1), world, max_over_ranks)
         K, flags = rast.gs_read_status(f, raise_on_error=False)
         if flags:
             raise RuntimeError(f"device status flags {flags} after timed loop ({mode})")
@@ -339,7 +375,7 @@ def run_ours(args):
     if dominant == "render":
         achieved = blend_flops / (st["render"] * 1e-3) / 1e12
         roof = {"kernel": "blend_kernel<16>", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": blend_traffic(K),
                 "work": {"evaluated_pairs": ev_pairs, "contributing_pairs": contrib_pairs, "flops": blend_flops,
                          "executed_pairs_after_culling": exec_pairs},
                 "peak_src": f"152 SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz"}
