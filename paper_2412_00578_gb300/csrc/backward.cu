@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : 2) blend_backward_kernel(c
                     const float q = fmaf(dx, fmaf(g0.z, dx, e), f);
                     if (q <= g1.y) {
                         has = true;
-                        const float g = gs_expf(-0.5f * q);
+                        const float g = gs_expf_blend(-0.5f * q);
                         const float raw = g1.z * g;
                         const float alpha = fminf(0.99f, raw);
                         const float Tb = Tr / (1.0f - alpha);

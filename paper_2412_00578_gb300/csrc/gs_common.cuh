@@ -11,7 +11,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/gs.h"
+#include "gs.h"  // include/ is on the compiler include path
 
 namespace gs {
 
@@ -124,6 +124,27 @@ __device__ __forceinline__ float gs_expf(float x) {
     p = fmaf(p, r, 1.0f);
     p = fmaf(p, r, 1.0f);
     return ldexpf(p, (int)k);
+}
+
+// gs_expf for the blend, where x = -q/2 with 0 <= q <= t <= 2 ln 255: the same
+// reduction and polynomial, with the final scaling by 2^k done as an add to
+// the exponent field, which is exactly ldexpf whenever the result is a normal
+// number (x >= -80 here).  Any other x takes gs_expf itself, so the value is
+// gs_expf(x) bit for bit for every input.
+__device__ __forceinline__ float gs_expf_blend(float x) {
+    if (!(x >= -80.0f && x <= 88.0f)) return gs_expf(x);
+    const float k = rintf(x * 1.44269502f);
+    float r = fmaf(-k, 0.693145751953125f, x);
+    r = fmaf(-k, 1.42860682030941723e-06f, r);
+    float p = 1.0f / 5040.0f;
+    p = fmaf(p, r, 1.0f / 720.0f);
+    p = fmaf(p, r, 1.0f / 120.0f);
+    p = fmaf(p, r, 1.0f / 24.0f);
+    p = fmaf(p, r, 1.0f / 6.0f);
+    p = fmaf(p, r, 0.5f);
+    p = fmaf(p, r, 1.0f);
+    p = fmaf(p, r, 1.0f);
+    return __int_as_float(__float_as_int(p) + ((int)k << 23));
 }
 
 // floor(x) as an int clamped to [lo, hi], safe for any finite or infinite x.

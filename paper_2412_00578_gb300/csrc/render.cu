@@ -123,19 +123,39 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : 2) blend_kernel(const Blen
     uint32_t last = 0;
     bool done = !inside;
     uint32_t stop_pos = 0, n_exec = 0, n_contrib = 0;
+    // Software pipeline over the batches: while the warps work on batch i,
+    // each loading thread already has batch i+1's 2D state in flight and
+    // batch i+2's index requested.
+    const bool loader = (int)threadIdx.x < NB;
+    uint32_t id_next = 0, id_next2 = 0;
+    float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0, q2 = q0;
+    if (loader) {
+        if ((int)threadIdx.x < n) {
+            const uint32_t id = A.vals[rg.x + threadIdx.x];
+            q0 = p0[id];
+            q1 = p1[id];
+            q2 = p2[id];
+        }
+        if (NB + (int)threadIdx.x < n) id_next = A.vals[rg.x + NB + threadIdx.x];
+    }
     for (int b0 = 0; b0 < n; b0 += NB) {
         if (__syncthreads_count(done) == NT) break;
-        const int j = b0 + (int)threadIdx.x;
-        if ((int)threadIdx.x < NB && j < n) {
-            const uint32_t id = A.vals[rg.x + j];
-            const float4 q0 = p0[id];
-            const float4 q1 = p1[id];
+        if (loader && b0 + (int)threadIdx.x < n) {
             s_g0[threadIdx.x] = make_float4(q0.x, q0.y, q1.x, q1.y + q1.y);
             s_g1[threadIdx.x] = make_float4(q1.z, q1.w, q0.z, 0.0f);
-            s_g2[threadIdx.x] = p2[id];
+            s_g2[threadIdx.x] = q2;
             s_mask[threadIdx.x] = subtile_mask<T>(q0.x, q0.y, q1.x, q1.y, q1.z, q1.w, ox, oy);
         }
         __syncthreads();
+        if (loader) {
+            if (b0 + NB + (int)threadIdx.x < n) {
+                q0 = p0[id_next];
+                q1 = p1[id_next];
+                q2 = p2[id_next];
+            }
+            if (b0 + 2 * NB + (int)threadIdx.x < n) id_next2 = A.vals[rg.x + b0 + 2 * NB + threadIdx.x];
+            id_next = id_next2;
+        }
         const int cnt = min(NB, n - b0);
         for (int c0 = 0; c0 < cnt; c0 += 32) {
             if (__all_sync(0xffffffffu, done)) break;
@@ -153,7 +173,7 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : 2) blend_kernel(const Blen
                 const float q = fmaf(dx, fmaf(g0.z, dx, e), f);
                 if (kStats) ++n_exec;
                 if (!(q <= g1.y)) continue;
-                const float g = gs_expf(-0.5f * q);
+                const float g = gs_expf_blend(-0.5f * q);
                 const float alpha = fminf(0.99f, g1.z * g);
                 const float Tn = Tr * (1.0f - alpha);
                 if (Tn < 1e-4f) {

@@ -105,22 +105,67 @@ struct PassArgs {
     int shift, dbits;
 };
 
+static_assert(kSortItems == 8, "a warp's 8 per-round digit counts are read as one 64-bit word");
+
+// Sum of the low r bytes of x (r <= 7, each byte <= 32, so the sum fits a byte).
+__device__ __forceinline__ uint32_t low_bytes_sum(unsigned long long x, int r) {
+    if (r == 0) return 0u;
+    const unsigned long long m = (r >= 8) ? ~0ull : ((1ull << (8 * r)) - 1ull);
+    return (uint32_t)(((x & m) * 0x0101010101010101ull) >> 56);
+}
+
 struct PassSmem {
     uint64_t keys[kSortPartition];
     uint32_t vals[kSortPartition];
-    uint32_t wcnt[kSortThreads / 32][256];
+    // per (warp, digit, round): how many of that round's 32 keys in that warp
+    // have that digit (at most 32)
+    uint8_t cnt[kSortThreads / 32][256][kSortItems];
+    // per (warp, digit): keys with that digit in earlier warps of the partition
+    uint16_t wpre[kSortThreads / 32][256];
     uint32_t boff[256];
     uint32_t gbase[256];
-    uint32_t warp_tmp[32];
+    unsigned long long warp_tmp[32];
     uint32_t part;
 };
+
+// Exclusive scan of one 64-bit value per thread over the block.
+__device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long long v, unsigned long long* s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (int)(blockDim.x >> 5);
+    unsigned long long inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = lane < nwarps ? s_warp[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nwarps) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const unsigned long long r = (warp > 0 ? s_warp[warp - 1] : 0ull) + inc - v;
+    __syncthreads();
+    return r;
+}
 
 __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PassSmem& S = *reinterpret_cast<PassSmem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) S.part = atomicAdd(A.ticket, 1u);
-    for (int i = tid; i < (kSortThreads / 32) * 256; i += kSortThreads) (&S.wcnt[0][0])[i] = 0;
+    {
+        uint4* c4 = reinterpret_cast<uint4*>(&S.cnt[0][0][0]);
+        constexpr int n4 = (int)(sizeof(S.cnt) / sizeof(uint4));
+#pragma unroll
+        for (int i = tid; i < n4; i += kSortThreads) c4[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
     __syncthreads();
     const uint32_t K = frame_keys(A.status);
     const uint32_t part = S.part;
@@ -134,7 +179,6 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
     // is input order.
     uint64_t key[kSortItems];
     uint32_t val[kSortItems];
-    uint32_t rank[kSortItems];
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const uint32_t idx = base + warp * (kSortItems * 32) + r * 32 + lane;
@@ -142,40 +186,62 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
         key[r] = ok ? A.kin[idx] : 0ull;
         val[r] = ok ? A.vin[idx] : 0u;
     }
-    // Stable ranking within the warp, round by round.
+    // Rank, rounds independent of each other: lanes with equal digits in a
+    // round find each other (match), their rank among themselves is the
+    // number of lower lanes, and the lowest one records the group's size for
+    // (warp, digit, round).
     const uint32_t lt_mask = (1u << lane) - 1u;
+    uint32_t dig[kSortItems], lt[kSortItems];
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const uint32_t idx = base + warp * (kSortItems * 32) + r * 32 + lane;
         const uint32_t d = idx < K ? (uint32_t)((key[r] >> A.shift) & mask) : kNoDigit;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = 0;
-        if (d != kNoDigit) before = S.wcnt[warp][d];
-        rank[r] = before + __popc(peers & lt_mask);
-        __syncwarp();
-        if (d != kNoDigit && (peers & lt_mask) == 0) S.wcnt[warp][d] = before + __popc(peers);
-        __syncwarp();
+        dig[r] = d;
+        lt[r] = __popc(peers & lt_mask);
+        if (d != kNoDigit && lt[r] == 0) S.cnt[warp][d][r] = (uint8_t)__popc(peers);
     }
     __syncthreads();
-    // Per digit (threads 0..255, thread t <-> digit t): warp-exclusive offsets,
-    // block total, look-back.  The other threads feed zeros to the block scans.
+    // Per digit (threads 0..255, thread t <-> digit t): exclusive prefix over
+    // the warps, block total, published aggregate (within a warp the rounds'
+    // counts are summed again when keys are placed).  The other threads feed
+    // zeros to the block scan.
     const uint32_t t = tid;
     const bool digit_thread = t < 256;
     uint32_t tot = 0;
     if (digit_thread) {
 #pragma unroll
         for (int w = 0; w < kSortThreads / 32; ++w) {
-            const uint32_t c = S.wcnt[w][t];
-            S.wcnt[w][t] = tot;
-            tot += c;
+            const unsigned long long c = *reinterpret_cast<const unsigned long long*>(&S.cnt[w][t][0]);
+            S.wpre[w][t] = (uint16_t)tot;
+            tot += low_bytes_sum(c, 7) + (uint32_t)(c >> 56);
         }
         st_relaxed_gpu(A.lookback + (size_t)part * 256 + t, (part == 0 ? kFlagPrefix : kFlagAgg) | tot);
         // clear this partition's row of the next pass's table (that table's last
         // user was the previous pass, which has completed)
         if (A.lookback_next) A.lookback_next[(size_t)part * 256 + t] = 0;
     }
-    const uint32_t boff = block_excl_scan_u32(tot, S.warp_tmp);
-    const uint32_t dstart = block_excl_scan_u32(digit_thread ? A.hist[t] : 0u, S.warp_tmp);
+    // one scan for both the block's digit offsets (low 16 bits, at most 4096)
+    // and the digits' global starts (high bits)
+    const unsigned long long packed =
+        ((unsigned long long)(digit_thread ? A.hist[t] : 0u) << 16) | (unsigned long long)tot;
+    const unsigned long long sc = block_excl_scan_u64(packed, S.warp_tmp);
+    const uint32_t boff = (uint32_t)(sc & 0xffffull);
+    const uint32_t dstart = (uint32_t)(sc >> 16);
+    if (digit_thread) S.boff[t] = boff;
+    __syncthreads();
+    // Stage in digit order (positions are block-local, so this does not wait
+    // for the look-back, and it frees the key registers before it).
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t d = dig[r];
+        if (d != kNoDigit) {
+            const unsigned long long c = *reinterpret_cast<const unsigned long long*>(&S.cnt[warp][d][0]);
+            const uint32_t pos = S.boff[d] + S.wpre[warp][d] + low_bytes_sum(c, r) + lt[r];
+            S.keys[pos] = key[r];
+            S.vals[pos] = val[r];
+        }
+    }
     if (digit_thread) {
         uint32_t prefix = 0;
         if (part > 0) {
@@ -214,20 +280,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
             }
             st_relaxed_gpu(A.lookback + (size_t)part * 256 + t, kFlagPrefix | (prefix + tot));
         }
-        S.boff[t] = boff;
         S.gbase[t] = dstart + prefix - boff;  // modular: gbase + staging index = output index
-    }
-    __syncthreads();
-    // Stage in digit order.
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        const uint32_t idx = base + warp * (kSortItems * 32) + r * 32 + lane;
-        if (idx < K) {
-            const uint32_t d = (uint32_t)((key[r] >> A.shift) & mask);
-            const uint32_t pos = S.boff[d] + S.wcnt[warp][d] + rank[r];
-            S.keys[pos] = key[r];
-            S.vals[pos] = val[r];
-        }
     }
     __syncthreads();
     const uint32_t nvalid = min((uint32_t)kSortPartition, K - base);
