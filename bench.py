@@ -72,7 +72,7 @@ def dist_env():
 
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
-    """Samples SM clock / power / throttle reasons with nvidia-smi every 200 ms."""
+    """Samples SM clock / power / throttle reasons with nvidia-smi every 50 ms."""
 
     FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -88,9 +88,17 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                                          "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def count(self) -> int:
+        try:
+            self.fh.flush()
+            with open(self.path) as f:
+                return sum(1 for _ in f)
+        except Exception:
+            return 0
 
     def stop(self):
         if self.proc is None:
@@ -293,6 +301,12 @@ def run_ours(args):
             rast.gs_forward(scene, cam, cfg, f)
         e1.record(stream)
         barrier()
+        if sampler:  # keep the same load running (untimed) until the sampler has >= 5 samples
+            t_end = time.time() + 2.0
+            while sampler.count() < 5 and time.time() < t_end:
+                for _ in range(20):
+                    rast.gs_forward(scene, cam, cfg, f)
+                torch.cuda.synchronize(dev)
         clocks = sampler.stop() if sampler else None
         launches = rast.launch_count() - l0
         _, ms = replica_rate(steps, e0.elapsed_time(e1), world, max_over_ranks)
@@ -331,10 +345,43 @@ def run_ours(args):
     except Exception:
         bus = None
 
+    def timed_graph(mode, steps):
+        """The same frame captured once as a CUDA graph and replayed."""
+        cfg = raster.cfg_struct(args.tile, mode)
+        f = frames[mode]
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            rast.set_stream(side)
+            rast.gs_forward(scene, cam, cfg, f)
+            side.synchronize()
+            with torch.cuda.graph(g, stream=side):
+                rast.gs_forward(scene, cam, cfg, f)
+        rast.set_stream(stream)
+        stream.wait_stream(side)
+        for _ in range(3):
+            g.replay()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            g.replay()
+        e1.record(stream)
+        barrier()
+        _, ms = replica_rate(steps, e0.elapsed_time(e1), world, max_over_ranks)
+        K, flags = rast.gs_read_status(f, raise_on_error=False)
+        if flags:
+            raise RuntimeError(f"device status flags {flags} after graph replays ({mode})")
+        return ms
+
     # --- headline: AccuTile, K timed frames
     sampler = ClockSampler(None)
     ms_acc, launches, clocks = timed("accutile", args.steps, args.warmup, sampler)
     per_mode = {"accutile": {"ms_per_frame": ms_acc, "fps": 1e3 / ms_acc, "keys": keys["accutile"]}}
+    ms_graph = timed_graph("accutile", args.steps)
+    per_mode["accutile"]["ms_per_frame_cuda_graph"] = ms_graph
     for m in modes[1:]:
         ms, _, _ = timed(m, max(10, args.steps // 2), args.warmup)
         per_mode[m] = {"ms_per_frame": ms, "fps": 1e3 / ms, "keys": keys[m]}

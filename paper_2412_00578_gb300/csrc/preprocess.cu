@@ -3,7 +3,8 @@
 // Reads the planar parameter arrays with coalesced 4-byte loads (a warp reads
 // 128 contiguous bytes of each plane), computes the 2D state and the tile
 // count of the requested mode, and only for Gaussians that touch at least one
-// tile reads the SH coefficients (192 of the 236 bytes of a Gaussian) and
+// tile reads the SH coefficients (192 of the 236 bytes of a Gaussian; they are
+// prefetched into L2 at the start so the late loads do not wait on HBM) and
 // writes the 48-byte 2D state.  Gaussians that are culled or off-screen cost
 // their 40 bytes of geometry and opacity plus a 4-byte count.
 #include "tiles.cuh"
@@ -77,6 +78,10 @@ __device__ __forceinline__ void preprocess_one(const PreArgs& A, const CamK& C, 
         const float qw = __ldg(A.rots + i), qx = __ldg(A.rots + n + i), qy = __ldg(A.rots + 2 * n + i),
                     qz = __ldg(A.rots + 3 * n + i);
         const float sigma = __ldg(A.opac + i);
+        // Start moving this Gaussian's SH coefficients into L2 now: their loads
+        // come after the long geometry computation and then hit L2.
+        for (int k = 0; k < 3 * A.sh_coeffs; ++k)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(A.sh + (int64_t)k * n + i));
         bool ok = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(s0) && isfinite(s1) && isfinite(s2) &&
                   isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) && isfinite(sigma);
         // view transform

@@ -65,33 +65,6 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const HistArgs A) {
         if (sh[i]) atomicAdd(&A.hist[i], sh[i]);
 }
 
-// Exclusive scan of one value per thread over the block (up to 1024 threads).
-__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* s_warp) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = (int)(blockDim.x >> 5);
-    uint32_t inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_warp[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t w = lane < nwarps ? s_warp[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < nwarps) s_warp[lane] = w;
-    }
-    __syncthreads();
-    const uint32_t r = (warp > 0 ? s_warp[warp - 1] : 0u) + inc - v;
-    __syncthreads();
-    return r;
-}
-
 struct PassArgs {
     const uint64_t* kin;
     const uint32_t* vin;
