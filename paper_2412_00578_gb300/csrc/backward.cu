@@ -48,7 +48,7 @@ struct BwdArgs {
 };
 
 template <int T>
-__global__ void __launch_bounds__(T* T, T == 32 ? 1 : 2) blend_backward_kernel(const BwdArgs A) {
+__global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_backward_kernel(const BwdArgs A) {
     constexpr int NT = T * T;
     constexpr int NB = NT < 256 ? NT : 256;
     constexpr int NSX = T / kSubW;

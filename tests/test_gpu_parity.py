@@ -136,6 +136,24 @@ def test_orbit_camera_large_splats(raster, rast):
         check_against_oracle(gpu, scene, cam, mode, 16, bg=(0.5, 0.5, 0.5))
 
 
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_needles_and_faint_splats(raster, rast, tile):
+    """Long thin splats at every orientation (conics from round to nearly
+    singular) and faint ones (threshold t near 0, ellipses smaller than a
+    pixel): the blend's per-warp culling must keep every pixel the per-pixel
+    test accepts, so images and last-contributor indices stay bit-exact."""
+    scene = synth.uniform_box_scene(6000, seed=41, half=2.0, log_scale_mu=-3.5, log_scale_sd=0.5)
+    gen = torch.Generator().manual_seed(42)
+    stretch = torch.exp(4.0 * torch.rand(6000, generator=gen))  # 1 .. 55 x
+    scene.scales[0] *= stretch
+    scene.scales[1] /= stretch
+    faint = torch.rand(6000, generator=gen) < 0.3
+    scene.opacities[faint] = 0.004 + 0.02 * torch.rand(int(faint.sum()), generator=gen)
+    cam = synth.look_at(163, 119, 55.0, (0.7, -0.4, -5.5), (0.0, 0.0, 0.0))
+    gpu = run_pipeline(raster, rast, scene, cam, 2, tile, bg=(0.3, 0.1, 0.2))
+    check_against_oracle(gpu, scene, cam, 2, tile, bg=(0.3, 0.1, 0.2))
+
+
 @pytest.mark.parametrize("deg", [0, 1, 2])
 def test_sh_degrees(raster, rast, deg):
     scene, cam = ragged_case(n=1500, seed=33)
