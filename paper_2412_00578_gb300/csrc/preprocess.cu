@@ -4,8 +4,8 @@
 // 128 contiguous bytes of each plane), computes the 2D state and the tile
 // count of the requested mode, and only for Gaussians that touch at least one
 // tile reads the SH coefficients (192 of the 236 bytes of a Gaussian; they are
-// prefetched into L2 at the start so the late loads do not wait on HBM) and
-// writes the 48-byte 2D state.  Gaussians that are culled or off-screen cost
+// prefetched into L2 early, one prefetch per line and warp, so the late loads
+// do not wait on HBM) and writes the 48-byte 2D state.  Gaussians that are culled or off-screen cost
 // their 40 bytes of geometry and opacity plus a 4-byte count.
 #include "tiles.cuh"
 
@@ -78,16 +78,39 @@ __device__ __forceinline__ void preprocess_one(const PreArgs& A, const CamK& C, 
         const float qw = __ldg(A.rots + i), qx = __ldg(A.rots + n + i), qy = __ldg(A.rots + 2 * n + i),
                     qz = __ldg(A.rots + 3 * n + i);
         const float sigma = __ldg(A.opac + i);
-        // Start moving this Gaussian's SH coefficients into L2 now: their loads
-        // come after the long geometry computation and then hit L2.
-        for (int k = 0; k < 3 * A.sh_coeffs; ++k)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(A.sh + (int64_t)k * n + i));
         bool ok = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(s0) && isfinite(s1) && isfinite(s2) &&
                   isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) && isfinite(sigma);
         // view transform
         const float px = ((C.V[0] * mx + C.V[1] * my) + C.V[2] * mz) + C.V[3];
         const float py = ((C.V[4] * mx + C.V[5] * my) + C.V[6] * mz) + C.V[7];
         const float pz = ((C.V[8] * mx + C.V[9] * my) + C.V[10] * mz) + C.V[11];
+        // Start moving the SH coefficients of Gaussians that may be seen into
+        // L2 now: their loads come after the long geometry computation and
+        // then hit L2.  A warp's 32 Gaussians share each coefficient plane's
+        // 128-byte line(s), so its lanes split the prefetches of the first and
+        // last Gaussian's address in every plane; a warp whose Gaussians all
+        // lie behind the camera or far outside the view prefetches nothing.
+        // (Performance only: every colour is still read from memory.)
+        {
+            const bool maybe = pz > C.near_z && fabsf(px) < (3.0f * C.limx) * pz && fabsf(py) < (3.0f * C.limy) * pz;
+            const unsigned act = __activemask();
+            const unsigned want = __ballot_sync(act, maybe);
+            const int planes = 3 * A.sh_coeffs;
+            if (act == 0xffffffffu) {
+                if (want) {
+                    const int lane = (int)(threadIdx.x & 31);
+                    const int64_t first = i - lane;
+                    const int64_t last = min(first + 31, n - 1);
+                    for (int m = lane; m < 2 * planes; m += 32) {
+                        const float* a = A.sh + (int64_t)(m >> 1) * n + ((m & 1) ? last : first);
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+                    }
+                }
+            } else if (maybe) {
+                for (int k = 0; k < planes; ++k)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(A.sh + (int64_t)k * n + i));
+            }
+        }
         ok = ok && (pz > C.near_z);
         const float n2 = ((qw * qw + qx * qx) + qy * qy) + qz * qz;
         ok = ok && (n2 > 0.0f);

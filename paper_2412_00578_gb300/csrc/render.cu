@@ -77,7 +77,7 @@ __device__ __forceinline__ int camera_of_tile(const CamRec* table, int num_cams,
 }
 
 template <int T, bool kStats, bool kMulti>
-__global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 5 : 20)) blend_kernel(const BlendArgs A) {
+__global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 4 : 16)) blend_kernel(const BlendArgs A) {
     constexpr int NT = T * T;
     constexpr int NB = NT < 256 ? NT : 256;  // Gaussians per shared-memory batch
     constexpr int NSX = T / kSubW;

@@ -33,7 +33,8 @@ def rast(raster):
     return raster.Rasterizer("cuda:0")
 
 
-def run_pipeline(raster, rast, scene, cam, mode, tile, bg=(0.0, 0.0, 0.0), n_capacity=None, key_capacity=None):
+def run_pipeline(raster, rast, scene, cam, mode, tile, bg=(0.0, 0.0, 0.0), n_capacity=None, key_capacity=None,
+                 sort_digit_bits=0):
     """Run the five stages through the C ABI, snapshotting each stage's output."""
     dev_scene = scene.to("cuda:0")
     n = scene.n
@@ -41,7 +42,7 @@ def run_pipeline(raster, rast, scene, cam, mode, tile, bg=(0.0, 0.0, 0.0), n_cap
     if key_capacity is None:
         key_capacity = max(oracle.count_keys(scene, cam, tile, mode, prec64=False), 1)
     frame = raster.Frame(ncap, cam.width, cam.height, tile, key_capacity, "cuda:0")
-    cfg = raster.cfg_struct(tile, mode, bg)
+    cfg = raster.cfg_struct(tile, mode, bg, sort_digit_bits)
     out = {}
     rast.gs_preprocess(dev_scene, cam, cfg, frame)
     torch.cuda.synchronize()
@@ -152,6 +153,45 @@ def test_needles_and_faint_splats(raster, rast, tile):
     cam = synth.look_at(163, 119, 55.0, (0.7, -0.4, -5.5), (0.0, 0.0, 0.0))
     gpu = run_pipeline(raster, rast, scene, cam, 2, tile, bg=(0.3, 0.1, 0.2))
     check_against_oracle(gpu, scene, cam, 2, tile, bg=(0.3, 0.1, 0.2))
+
+
+def crowded_tile_case(n, seed):
+    """n tiny Gaussians whose centres project inside tile (1, 1) of a 64x48
+    image at tile 16 (pixels 16..31), half of them at one depth, so one
+    bucket holds every key and depth ties are broken by Gaussian index."""
+    scene = synth.uniform_box_scene(n, seed=seed, half=0.2, log_scale_mu=-7.0, log_scale_sd=0.3)
+    scene.means[0] -= 0.9
+    scene.means[1] += 0.06
+    same = torch.arange(n) % 2 == 0
+    scene.means[2, same] = 0.125
+    cam = synth.pinhole(64, 48, 60.0, np.eye(3), np.array([0.0, 0.0, 5.0]))
+    return scene, cam
+
+
+@pytest.mark.parametrize("n", [6000, 40000])
+def test_one_crowded_tile(raster, rast, n):
+    """One tile holding 6000 or 40000 keys (a digit run far longer than a sort
+    partition), half of them at one depth, so ties must keep Gaussian index
+    order; keys, values, ranges and image as the oracle."""
+    scene, cam = crowded_tile_case(n, seed=51)
+    _, counts = oracle.preprocess(scene, cam, 16, 2, prec64=False)
+    K = int(counts.sum())
+    assert K > 0.99 * n and counts.max() == 1  # precondition: at most one tile per Gaussian
+    gpu = run_pipeline(raster, rast, scene, cam, 2, 16)
+    ref = check_against_oracle(gpu, scene, cam, 2, 16)
+    r = ref["ranges"].reshape(-1, 2)
+    assert r[1 * 4 + 1, 1] - r[1 * 4 + 1, 0] == K  # all of them in tile (1, 1)
+
+
+@pytest.mark.parametrize("digits", [6, 5, 4])
+def test_digit_widths_agree(raster, rast, digits):
+    """Narrower radix digits (more passes) give the same sorted pairs, bit for
+    bit, as the default 8-bit digits."""
+    for scene, cam, mode in [(*ragged_case(), 0), (*crowded_tile_case(6000, seed=52), 2)]:
+        a = run_pipeline(raster, rast, scene, cam, mode, 16)
+        b = run_pipeline(raster, rast, scene, cam, mode, 16, sort_digit_bits=digits)
+        for k in ("keys", "vals", "ranges", "image", "last"):
+            assert np.array_equal(a[k], b[k]), k
 
 
 @pytest.mark.parametrize("deg", [0, 1, 2])
