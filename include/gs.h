@@ -193,8 +193,9 @@ gs_status gs_render(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* 
  * also counts, over all pixels: *evaluated = the (pixel, Gaussian) pairs the
  * tile-list definition evaluates (each entry of the pixel's tile list up to
  * and including the one that stops the pixel), *contributed = the pairs that
- * add to the colour, *executed = the pairs whose q the kernel actually
- * computed after its in-tile culling.  Synchronises the stream; host
+ * add to the colour, *executed = the pairs whose in-ellipse test the kernel
+ * actually evaluated after its in-tile culling (a pixel that stops part-way
+ * through a 256-entry batch has the rest of that batch tested too).  Synchronises the stream; host
  * outputs, nullable.  States the blend's algorithmic work; not for timing. */
 gs_status gs_render_stats(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame,
                           uint64_t* evaluated, uint64_t* contributed, uint64_t* executed);

@@ -7,10 +7,12 @@
 // pixel sub-tile.  The tile's Gaussians are brought into shared memory in
 // batches of one per thread (a gather of the 48-byte 2D state by sorted
 // index); the loading thread also computes which sub-tiles the Gaussian's
-// ellipse can reach, and each warp then walks, in depth order, only the
-// Gaussians whose mask has its bit (ballot + find-first-set), so warps skip
-// the many tile entries that lie elsewhere in the tile.  Every pixel still
-// evaluates every Gaussian that can reach it in the same order with the same
+// ellipse can reach.  Each warp then takes a batch in two phases: it walks,
+// in depth order, only the Gaussians whose mask has its bit (ballot +
+// find-first-set) and records per pixel which of them pass the in-ellipse
+// test; then every lane blends its own passing Gaussians in order, the lanes
+// of the warp working on different Gaussians at once.  Every pixel still
+// takes every Gaussian that reaches it in the same order with the same
 // arithmetic.  Per pixel (Eqs. render_alpha, 2d_gaussian_scalar,
 // contribution): dx = px - u, dy = py - v, e = (2b) dy, f = (c dy) dy,
 // q = fma(dx, fma(a, dx, e), f); a Gaussian counts iff q <= t (alpha >= 1/255);
@@ -85,6 +87,7 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 4 : 16)) blend_
     __shared__ float4 s_g1[NB];  // c, t, opacity, -
     __shared__ float4 s_g2[NB];  // r, g, b, -
     __shared__ uint32_t s_mask[NB];
+    __shared__ uint32_t s_pass[NT / 32][NB / 32][32];  // per warp, chunk, lane: passing entries
     const int tile = blockIdx.x;  // global tile index
     int gx = A.gx, width = A.width, height = A.height, local = tile;
     float* image = A.image;
@@ -156,41 +159,70 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 4 : 16)) blend_
             if (b0 + 2 * NB + (int)threadIdx.x < n) id_next2 = A.vals[rg.x + b0 + 2 * NB + threadIdx.x];
             id_next = id_next2;
         }
+        if (__all_sync(0xffffffffu, done)) continue;
         const int cnt = min(NB, n - b0);
-        for (int c0 = 0; c0 < cnt; c0 += 32) {
-            if (__all_sync(0xffffffffu, done)) break;
+        const int nch = (cnt + 31) >> 5;
+        // Phase 1: the in-ellipse test of every entry whose mask reaches this
+        // warp's sub-tile, for every pixel still running; bit j of chunk c
+        // records that entry 32 c + j passes for this lane's pixel.
+        for (int c = 0; c < nch; ++c) {
+            const int c0 = c * 32;
             uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && (s_mask[c0 + lane] & my_bit));
+            uint32_t pass = 0;
             while (bits) {
-                const int k = c0 + __ffs(bits) - 1;
+                const int j = __ffs(bits) - 1;
                 bits &= bits - 1u;
                 if (done) continue;
-                const float4 g0 = s_g0[k];
-                const float4 g1 = s_g1[k];
+                const float4 g0 = s_g0[c0 + j];
+                const float4 g1 = s_g1[c0 + j];
                 const float dx = pxf - g0.x;
                 const float dy = pyf - g0.y;
                 const float e = g0.w * dy;
                 const float f = (g1.x * dy) * dy;
                 const float q = fmaf(dx, fmaf(g0.z, dx, e), f);
                 if (kStats) ++n_exec;
-                if (!(q <= g1.y)) continue;
-                const float g = gs_expf_blend(-0.5f * q);
-                const float alpha = fminf(0.99f, g1.z * g);
-                const float Tn = Tr * (1.0f - alpha);
-                if (Tn < 1e-4f) {
-                    done = true;
-                    stop_pos = (uint32_t)(b0 + k + 1);
-                    continue;
-                }
-                const float w = alpha * Tr;
-                const float4 col = s_g2[k];
-                C0 = fmaf(col.x, w, C0);
-                C1 = fmaf(col.y, w, C1);
-                C2 = fmaf(col.z, w, C2);
-                Tr = Tn;
-                last = (uint32_t)(b0 + k + 1);
-                if (kStats) ++n_contrib;
+                if (q <= g1.y) pass |= 1u << j;
             }
+            s_pass[warp][c][lane] = pass;
         }
+        __syncwarp();
+        // Phase 2: each lane blends its own passing entries in list order (q
+        // recomputed with the same operations) until its pixel stops, so the
+        // warp's iterations follow its busiest pixel, not the union of all.
+        int c = 0;
+        uint32_t cur = s_pass[warp][0][lane];
+        for (;;) {
+            while (cur == 0u && c + 1 < nch) cur = s_pass[warp][++c][lane];
+            const bool have = cur != 0u && !done;
+            if (!__any_sync(0xffffffffu, have)) break;
+            if (!have) continue;
+            const int k = c * 32 + __ffs(cur) - 1;
+            cur &= cur - 1u;
+            const float4 g0 = s_g0[k];
+            const float4 g1 = s_g1[k];
+            const float dx = pxf - g0.x;
+            const float dy = pyf - g0.y;
+            const float e = g0.w * dy;
+            const float f = (g1.x * dy) * dy;
+            const float q = fmaf(dx, fmaf(g0.z, dx, e), f);
+            const float g = gs_expf_blend(-0.5f * q);
+            const float alpha = fminf(0.99f, g1.z * g);
+            const float Tn = Tr * (1.0f - alpha);
+            if (Tn < 1e-4f) {
+                done = true;
+                stop_pos = (uint32_t)(b0 + k + 1);
+                continue;
+            }
+            const float w = alpha * Tr;
+            const float4 col = s_g2[k];
+            C0 = fmaf(col.x, w, C0);
+            C1 = fmaf(col.y, w, C1);
+            C2 = fmaf(col.z, w, C2);
+            Tr = Tn;
+            last = (uint32_t)(b0 + k + 1);
+            if (kStats) ++n_contrib;
+        }
+        __syncwarp();
     }
     if (inside) {
         const size_t HW = (size_t)width * height;
