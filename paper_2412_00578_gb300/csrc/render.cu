@@ -48,6 +48,8 @@ __global__ void __launch_bounds__(256) ranges_kernel(const uint64_t* __restrict_
     if (i == K - 1) ranges[tile].y = K;
 }
 
+constexpr unsigned kMaxOrderedTiles = 1u << 16;  // beyond this the blend runs tiles in index order
+
 struct BlendArgs {
     const uint2* ranges;
     const uint32_t* vals;
@@ -64,6 +66,7 @@ struct BlendArgs {
     int num_cams;
     int64_t cam_stride;
     int64_t pixel_capacity;
+    const uint32_t* order;      // tile of each CTA (heaviest first), or nullptr for tile = CTA
 };
 
 // Camera owning global tile g of a multi-view batch: the last camera whose
@@ -78,6 +81,40 @@ __device__ __forceinline__ int camera_of_tile(const CamRec* table, int num_cams,
     return lo;
 }
 
+// Launch order of the blend's tiles, heaviest first: a counting sort of the
+// tiles by floor(log2(entries)), descending (one block).  Tiles are
+// independent, so the order changes only when each tile's CTA starts; it keeps
+// the few tiles with thousands of entries from starting last and leaving the
+// rest of the GPU idle while they finish.
+__global__ void __launch_bounds__(1024) tile_order_kernel(const uint2* __restrict__ ranges, uint32_t tiles,
+                                                         uint32_t* __restrict__ order) {
+    __shared__ uint32_t cnt[33];
+    __shared__ uint32_t base[33];
+    if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        const uint32_t n = r.y - r.x;
+        const uint32_t cls = n ? 32u - (uint32_t)__clz(n) : 0u;  // 0..32, larger = more entries
+        atomicAdd(&cnt[32 - cls], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int k = 0; k < 33; ++k) {
+            base[k] = run;
+            run += cnt[k];
+        }
+    }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        const uint32_t n = r.y - r.x;
+        const uint32_t cls = n ? 32u - (uint32_t)__clz(n) : 0u;
+        order[atomicAdd(&base[32 - cls], 1u)] = t;
+    }
+}
+
 template <int T, bool kStats, bool kMulti>
 __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 4 : 16)) blend_kernel(const BlendArgs A) {
     constexpr int NT = T * T;
@@ -88,7 +125,7 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 4 : 16)) blend_
     __shared__ float4 s_g2[NB];  // r, g, b, -
     __shared__ uint32_t s_mask[NB];
     __shared__ uint32_t s_pass[NT / 32][NB / 32][32];  // per warp, chunk, lane: passing entries
-    const int tile = blockIdx.x;  // global tile index
+    const int tile = A.order ? (int)A.order[blockIdx.x] : (int)blockIdx.x;  // global tile index
     int gx = A.gx, width = A.width, height = A.height, local = tile;
     float* image = A.image;
     float* final_T = A.final_T;
@@ -283,6 +320,14 @@ gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameVi
     A.pixel_capacity = v.pixel_capacity;
     const unsigned tiles = (unsigned)(v.gx * v.gy);
     if (tiles == 0) return GS_OK;
+    // The order array lives in the sort's look-back table, idle until the next
+    // sort, which clears every word of it that it reads before reading it.
+    A.order = nullptr;
+    if (tiles <= kMaxOrderedTiles && (int64_t)tiles <= 2 * v.sort_partitions * 256) {
+        tile_order_kernel<<<1, 1024, 0, ctx->stream>>>(v.ranges, tiles, v.sort_lookback);
+        ctx->launches += 1;
+        A.order = v.sort_lookback;
+    }
 #define GS_BLEND_LAUNCH(T_, S_, M_) blend_kernel<T_, S_, M_><<<tiles, T_ * T_, 0, ctx->stream>>>(A)
 #define GS_BLEND_TILES(S_, M_)                                                             \
     switch (v.tile) {                                                                      \
