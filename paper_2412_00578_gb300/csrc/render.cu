@@ -82,7 +82,8 @@ __device__ __forceinline__ int camera_of_tile(const CamRec* table, int num_cams,
 }
 
 // Launch order of the blend's tiles, heaviest first: a counting sort of the
-// tiles by floor(log2(entries)), descending (one block).  Tiles are
+// tiles by floor(log2(entries)), descending (one block, one shared-memory
+// atomic per warp and class).  Tiles are
 // independent, so the order changes only when each tile's CTA starts; it keeps
 // the few tiles with thousands of entries from starting last and leaving the
 // rest of the GPU idle while they finish.
@@ -90,13 +91,17 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const uint2* __restric
                                                          uint32_t* __restrict__ order) {
     __shared__ uint32_t cnt[33];
     __shared__ uint32_t base[33];
+    const uint32_t lane = threadIdx.x & 31u;
     if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < tiles; t += blockDim.x) {
-        const uint2 r = ranges[t];
-        const uint32_t n = r.y - r.x;
-        const uint32_t cls = n ? 32u - (uint32_t)__clz(n) : 0u;  // 0..32, larger = more entries
-        atomicAdd(&cnt[32 - cls], 1u);
+    // Class 0 = heaviest (32 - floor(log2(n)) - 1), 32 = empty; lanes of a
+    // warp with the same class add to its counter once.
+    for (uint32_t t0 = 0; t0 < tiles; t0 += blockDim.x) {
+        const uint32_t t = t0 + threadIdx.x;
+        const uint32_t n = t < tiles ? ranges[t].y - ranges[t].x : 0u;
+        const uint32_t cls = n ? (uint32_t)__clz(n) : 32u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, t < tiles ? cls : 64u);
+        if (t < tiles && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&cnt[cls], (uint32_t)__popc(peers));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -107,11 +112,16 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const uint2* __restric
         }
     }
     __syncthreads();
-    for (uint32_t t = threadIdx.x; t < tiles; t += blockDim.x) {
-        const uint2 r = ranges[t];
-        const uint32_t n = r.y - r.x;
-        const uint32_t cls = n ? 32u - (uint32_t)__clz(n) : 0u;
-        order[atomicAdd(&base[32 - cls], 1u)] = t;
+    for (uint32_t t0 = 0; t0 < tiles; t0 += blockDim.x) {
+        const uint32_t t = t0 + threadIdx.x;
+        const uint32_t n = t < tiles ? ranges[t].y - ranges[t].x : 0u;
+        const uint32_t cls = n ? (uint32_t)__clz(n) : 32u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, t < tiles ? cls : 64u);
+        const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
+        uint32_t b = 0;
+        if (t < tiles && lane == leader) b = atomicAdd(&base[cls], (uint32_t)__popc(peers));
+        b = __shfl_sync(0xffffffffu, b, leader);
+        if (t < tiles) order[b + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = t;
     }
 }
 
