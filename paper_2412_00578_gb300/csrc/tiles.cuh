@@ -17,8 +17,11 @@ struct Ellipse {
 };
 
 struct Grid {
-    float T;      // tile edge, pixels
+    float T;      // tile edge, pixels (8, 16 or 32)
     int gx, gy;   // tiles per row, per column
+    // 1/T.  T is a power of two, so x * invT is the exactly scaled x / T,
+    // bit for bit the IEEE quotient, at the cost of one multiply.
+    __host__ __device__ float invT() const { return T == 8.0f ? 0.125f : (T == 16.0f ? 0.0625f : 0.03125f); }
 };
 
 // 3D-GS rectangle: min = trunc((mu - r)/T), max (exclusive) =
@@ -35,10 +38,10 @@ struct Rect {
 
 __device__ __forceinline__ bool sigma3_rect(float u, float v, int radius, const Grid& g, Rect& R) {
     const float r = (float)radius;
-    R.x0 = trunc_clamp((u - r) / g.T, g.gx);
-    R.x1 = trunc_clamp(((u + r) + (g.T - 1.0f)) / g.T, g.gx) - 1;
-    R.y0 = trunc_clamp((v - r) / g.T, g.gy);
-    R.y1 = trunc_clamp(((v + r) + (g.T - 1.0f)) / g.T, g.gy) - 1;
+    R.x0 = trunc_clamp((u - r) * g.invT(), g.gx);
+    R.x1 = trunc_clamp(((u + r) + (g.T - 1.0f)) * g.invT(), g.gx) - 1;
+    R.y0 = trunc_clamp((v - r) * g.invT(), g.gy);
+    R.y1 = trunc_clamp(((v + r) + (g.T - 1.0f)) * g.invT(), g.gy) - 1;
     return R.x1 >= R.x0 && R.y1 >= R.y0;
 }
 
@@ -63,10 +66,10 @@ __device__ __forceinline__ bool snugbox(const Ellipse& E, const Grid& g, Snug& S
     S.y1 = E.v + S.hy;
     if (!(S.x1 >= 0.0f) || !(S.y1 >= 0.0f) || !(S.x0 < (float)g.gx * g.T) || !(S.y0 < (float)g.gy * g.T))
         return false;
-    S.R.x0 = floor_clamp(S.x0 / g.T, 0, g.gx - 1);
-    S.R.x1 = floor_clamp(S.x1 / g.T, 0, g.gx - 1);
-    S.R.y0 = floor_clamp(S.y0 / g.T, 0, g.gy - 1);
-    S.R.y1 = floor_clamp(S.y1 / g.T, 0, g.gy - 1);
+    S.R.x0 = floor_clamp(S.x0 * g.invT(), 0, g.gx - 1);
+    S.R.x1 = floor_clamp(S.x1 * g.invT(), 0, g.gx - 1);
+    S.R.y0 = floor_clamp(S.y0 * g.invT(), 0, g.gy - 1);
+    S.R.y1 = floor_clamp(S.y1 * g.invT(), 0, g.gy - 1);
     return true;
 }
 
@@ -136,8 +139,8 @@ __device__ __forceinline__ int accutile_sweep(const Ellipse& E, const Snug& S, c
         else if (have_lo) emax = lo_r;
         else if (have_hi) emax = hi_r;
         else emax = e_hi;
-        const float qmin = emin / g.T;
-        const float qmax = emax / g.T;
+        const float qmin = emin * g.invT();
+        const float qmax = emax * g.invT();
         const float fmn = floorf(qmin);
         const float fmx = floorf(qmax);
         const int jmin = floor_clamp(qmin, j0, j1);
