@@ -143,47 +143,75 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
     // (one per thread), so the 2D-state loads of a round are coalesced and
     // neighbouring threads write neighbouring key ranges.  A slot is a
     // Gaussian (single view) or a (camera, Gaussian) pair, camera-major.
+    // Software pipeline: the four rounds' counts are loaded up front, and
+    // while a round is processed the next round's 2D state is already in
+    // flight, so the rounds do not wait on memory one after another.
     long long carry = A.partials[blockIdx.x];
     const int64_t block0 = (int64_t)blockIdx.x * kScanBlock;
-#pragma unroll 1
+    int cnt[kScanItems];
+#pragma unroll
     for (int r = 0; r < kScanItems; ++r) {
         const int64_t i = block0 + (int64_t)r * kScanThreads + threadIdx.x;
-        const int c = i < A.n ? A.counts[i] : 0;
+        cnt[r] = i < A.n ? A.counts[i] : 0;
+    }
+    const bool three = A.mode == GS_MODE_3SIGMA;
+    float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
+    int rad = 0;
+    if (cnt[0] > 0) {
+        const int64_t i = block0 + threadIdx.x;
+        q0 = A.p0[i];
+        if (three) rad = __float_as_int(A.p2[i].w);
+        else q1 = A.p1[i];
+    }
+#pragma unroll
+    for (int r = 0; r < kScanItems; ++r) {
+        const int64_t i = block0 + (int64_t)r * kScanThreads + threadIdx.x;
+        const int c = cnt[r];
+        float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+        int nrad = 0;
+        if (r + 1 < kScanItems && cnt[r + 1] > 0) {
+            const int64_t in = i + kScanThreads;
+            n0 = A.p0[in];
+            if (three) nrad = __float_as_int(A.p2[in].w);
+            else n1 = A.p1[in];
+        }
         long long total;
         const long long off = carry + block_excl_scan(c, s_warp, &total);
         __syncthreads();  // s_warp is reused by the next round's scan
         carry += total;
-        if (c == 0) continue;
-        Grid grid = A.grid;
-        uint32_t tile0 = 0, id = (uint32_t)i;
-        if (kMulti) {
-            const int64_t cam = i / A.cam_stride;
-            const CamRec& R = A.table[cam];
-            grid.gx = R.gx;
-            grid.gy = R.gy;
-            tile0 = (uint32_t)R.tile_offset;
-            id = (uint32_t)(i - cam * A.cam_stride);
-        }
-        const float4 q0 = A.p0[i];
-        KeyWriter W{A.keys, A.vals, off, off + c, __float_as_uint(q0.w), id, grid.gx, tile0};
-        if (A.mode == GS_MODE_3SIGMA) {
-            Rect R;
-            if (sigma3_rect(q0.x, q0.y, __float_as_int(A.p2[i].w), grid, R))
-                for (int ty = R.y0; ty <= R.y1; ++ty)
-                    for (int tx = R.x0; tx <= R.x1; ++tx) W.put((uint32_t)(ty * grid.gx + tx));
-        } else {
-            const float4 q1 = A.p1[i];
-            const Ellipse E{q0.x, q0.y, q1.x, q1.y, q1.z, q1.w};
-            Snug S;
-            if (snugbox(E, grid, S)) {
-                if (A.mode == GS_MODE_SNUGBOX) {
-                    for (int ty = S.R.y0; ty <= S.R.y1; ++ty)
-                        for (int tx = S.R.x0; tx <= S.R.x1; ++tx) W.put((uint32_t)(ty * grid.gx + tx));
-                } else {
-                    accutile_sweep(E, S, grid, W);
+        if (c > 0) {
+            Grid grid = A.grid;
+            uint32_t tile0 = 0, id = (uint32_t)i;
+            if (kMulti) {
+                const int64_t cam = i / A.cam_stride;
+                const CamRec& R = A.table[cam];
+                grid.gx = R.gx;
+                grid.gy = R.gy;
+                tile0 = (uint32_t)R.tile_offset;
+                id = (uint32_t)(i - cam * A.cam_stride);
+            }
+            KeyWriter W{A.keys, A.vals, off, off + c, __float_as_uint(q0.w), id, grid.gx, tile0};
+            if (three) {
+                Rect R;
+                if (sigma3_rect(q0.x, q0.y, rad, grid, R))
+                    for (int ty = R.y0; ty <= R.y1; ++ty)
+                        for (int tx = R.x0; tx <= R.x1; ++tx) W.put((uint32_t)(ty * grid.gx + tx));
+            } else {
+                const Ellipse E{q0.x, q0.y, q1.x, q1.y, q1.z, q1.w};
+                Snug S;
+                if (snugbox(E, grid, S)) {
+                    if (A.mode == GS_MODE_SNUGBOX) {
+                        for (int ty = S.R.y0; ty <= S.R.y1; ++ty)
+                            for (int tx = S.R.x0; tx <= S.R.x1; ++tx) W.put((uint32_t)(ty * grid.gx + tx));
+                    } else {
+                        accutile_sweep(E, S, grid, W);
+                    }
                 }
             }
         }
+        q0 = n0;
+        q1 = n1;
+        rad = nrad;
     }
 }
 
