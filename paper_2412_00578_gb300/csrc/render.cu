@@ -1,6 +1,6 @@
 // identifyTileRanges and render (Sec. 3.2.2, Sec. 3.2.3).
 //
-// ranges: one thread per sorted key; a thread whose tile differs from its
+// ranges: four sorted keys per thread; a key whose tile differs from its
 // predecessor's closes the previous range and opens its own.
 //
 // blend: one CTA per tile, one thread per pixel, each warp owning an 8 x 4
@@ -30,22 +30,42 @@ __device__ __forceinline__ uint32_t frame_keys_r(const uint32_t* status) {
     return ((status[2] & GS_FLAG_CAPACITY) || status[3]) ? 0u : status[0];
 }
 
+// Four consecutive keys per thread (two 16-byte loads when the buffer is
+// 16-byte aligned) plus the key before them: a key whose tile differs from its
+// predecessor's closes the previous range and opens its own.
 __global__ void __launch_bounds__(256) ranges_kernel(const uint64_t* __restrict__ keys,
                                                      const uint32_t* __restrict__ status, uint2* __restrict__ ranges) {
     const uint32_t K = frame_keys_r(status);
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= K) return;
-    const uint32_t tile = (uint32_t)(keys[i] >> 32);
-    if (i == 0) {
-        ranges[tile].x = 0;
+    const uint32_t i0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4u;
+    if (i0 >= K) return;
+    uint32_t t[4];
+    // the frame only guarantees 8-byte alignment of keys: vector loads only
+    // from a 16-byte aligned buffer
+    if (i0 + 4u <= K && (reinterpret_cast<uintptr_t>(keys) & 15u) == 0u) {
+        const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(keys + i0);
+        const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(keys + i0 + 2);
+        t[0] = (uint32_t)(a.x >> 32);
+        t[1] = (uint32_t)(a.y >> 32);
+        t[2] = (uint32_t)(b.x >> 32);
+        t[3] = (uint32_t)(b.y >> 32);
     } else {
-        const uint32_t prev = (uint32_t)(keys[i - 1] >> 32);
-        if (prev != tile) {
-            ranges[prev].y = i;
-            ranges[tile].x = i;
-        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) t[j] = i0 + j < K ? (uint32_t)(keys[i0 + j] >> 32) : 0u;
     }
-    if (i == K - 1) ranges[tile].y = K;
+    uint32_t prev = i0 > 0 ? (uint32_t)(keys[i0 - 1] >> 32) : 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t i = i0 + j;
+        if (i >= K) break;
+        if (i == 0) {
+            ranges[t[j]].x = 0;
+        } else if (prev != t[j]) {
+            ranges[prev].y = i;
+            ranges[t[j]].x = i;
+        }
+        if (i == K - 1) ranges[t[j]].y = K;
+        prev = t[j];
+    }
 }
 
 constexpr unsigned kMaxOrderedTiles = 1u << 16;  // beyond this the blend runs tiles in index order
@@ -301,7 +321,7 @@ gs_status launch_ranges(gs_context* ctx, const FrameView& v) {
     if (cudaMemsetAsync(v.ranges, 0, tiles * sizeof(uint2), ctx->stream) != cudaSuccess)
         return set_error(ctx, GS_ERR_CUDA, "tile_ranges: cudaMemsetAsync failed");
     if (v.kcap == 0) return GS_OK;
-    const int64_t blocks = (v.kcap + 255) / 256;
+    const int64_t blocks = (v.kcap + 1023) / 1024;  // 4 keys per thread
     ranges_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(v.keys0, v.status, v.ranges);
     ctx->launches += 1;
     return check_launch(ctx, "tile_ranges");
