@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) ranges_kernel(const uint64_t* __restrict_
     }
 }
 
-constexpr unsigned kMaxOrderedTiles = 1u << 16;  // beyond this the blend runs tiles in index order
+constexpr unsigned kMaxOrderedTiles = 1u << 15;  // beyond this the blend runs tiles in index order
 
 struct BlendArgs {
     const uint2* ranges;
@@ -111,16 +111,30 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const uint2* __restric
                                                          uint32_t* __restrict__ order) {
     __shared__ uint32_t cnt[33];
     __shared__ uint32_t base[33];
+    __shared__ uint8_t s_cls[kMaxOrderedTiles];  // class of each tile, read once from ranges
     const uint32_t lane = threadIdx.x & 31u;
     if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+    // Class 0 = heaviest (clz of the entry count), 32 = empty.
+    for (uint32_t t0 = 0; t0 < tiles; t0 += 4u * blockDim.x) {
+        uint2 r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t t = t0 + (uint32_t)u * blockDim.x + threadIdx.x;
+            r[u] = t < tiles ? ranges[t] : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t t = t0 + (uint32_t)u * blockDim.x + threadIdx.x;
+            const uint32_t n = r[u].y - r[u].x;
+            if (t < tiles) s_cls[t] = (uint8_t)(n ? __clz(n) : 32);
+        }
+    }
     __syncthreads();
-    // Class 0 = heaviest (32 - floor(log2(n)) - 1), 32 = empty; lanes of a
-    // warp with the same class add to its counter once.
+    // lanes of a warp with the same class add to its counter once
     for (uint32_t t0 = 0; t0 < tiles; t0 += blockDim.x) {
         const uint32_t t = t0 + threadIdx.x;
-        const uint32_t n = t < tiles ? ranges[t].y - ranges[t].x : 0u;
-        const uint32_t cls = n ? (uint32_t)__clz(n) : 32u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, t < tiles ? cls : 64u);
+        const uint32_t cls = t < tiles ? s_cls[t] : 64u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, cls);
         if (t < tiles && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&cnt[cls], (uint32_t)__popc(peers));
     }
     __syncthreads();
@@ -134,9 +148,8 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const uint2* __restric
     __syncthreads();
     for (uint32_t t0 = 0; t0 < tiles; t0 += blockDim.x) {
         const uint32_t t = t0 + threadIdx.x;
-        const uint32_t n = t < tiles ? ranges[t].y - ranges[t].x : 0u;
-        const uint32_t cls = n ? (uint32_t)__clz(n) : 32u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, t < tiles ? cls : 64u);
+        const uint32_t cls = t < tiles ? s_cls[t] : 64u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, cls);
         const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
         uint32_t b = 0;
         if (t < tiles && lane == leader) b = atomicAdd(&base[cls], (uint32_t)__popc(peers));

@@ -53,7 +53,18 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const HistArgs A) {
     const uint32_t K = frame_keys(A.status);
     const uint32_t mask = (1u << A.dbits) - 1u;
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += stride) {
+    // four keys per thread and step, all loaded before any is counted
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3u * stride < K; i += 4u * stride) {
+        uint64_t key[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) key[u] = A.keys[i + (uint32_t)u * stride];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            for (int p = 0; p < A.passes; ++p)
+                atomicAdd(&sh[p * 256 + (uint32_t)((key[u] >> (p * A.dbits)) & mask)], 1u);
+    }
+    for (; i < K; i += stride) {
         const uint64_t key = A.keys[i];
         for (int p = 0; p < A.passes; ++p) atomicAdd(&sh[p * 256 + (uint32_t)((key >> (p * A.dbits)) & mask)], 1u);
     }
