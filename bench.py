@@ -149,20 +149,35 @@ def peaks():
         return {"hbm_gbs": 6800.0, "src": "fallback", "sm_max_mhz": 2070.0}
 
 
+def blend_source_digest():
+    """sha256 over what determines the blend kernel's memory traffic: the
+    shared headers it includes, the kernel template itself and its launcher
+    (render.cu's other kernels are not part of it)."""
+    import hashlib
+
+    csrc = os.path.join(ROOT, "paper_2412_00578_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in ("blend_common.cuh", "gs_common.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    with open(os.path.join(csrc, "render.cu")) as f:
+        r = f.read()
+    a = r.index("struct BlendArgs {")
+    h.update(r[a:r.index("};", a)].encode())
+    a = r.index("template <int T, bool kStats, bool kMulti>")
+    h.update(r[a:r.index("}  // namespace", a)].encode())
+    h.update(r[r.index("gs_status launch_render("):].encode())
+    return h.hexdigest()
+
+
 def blend_traffic(keys):
     """DRAM bytes of one blend launch, from the ncu counters in
     profiles/dram_traffic.json scaled per key, or None if the blend's sources
     changed since those counters were taken."""
-    import hashlib
-
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
             rec = json.load(f)["blend_kernel"]
-        h = hashlib.sha256()
-        for p in rec["sources"]:
-            with open(os.path.join(ROOT, p), "rb") as f:
-                h.update(f.read())
-        if h.hexdigest() != rec["source_sha256"]:
+        if blend_source_digest() != rec["source_sha256"]:
             return None
         return rec["bytes_per_key"] * keys
     except Exception:
