@@ -30,7 +30,7 @@ constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
 constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr uint32_t kNoDigit = 0xffffffffu;
-constexpr int kLookWindow = 8;  // predecessors inspected per look-back step
+constexpr int kLookWindow = 16;  // predecessors inspected per look-back step
 
 // Keys present in the buffer: none when the emit was skipped (keys over
 // capacity, or batch cameras over the frame's tile/pixel capacity).
