@@ -249,19 +249,25 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 4 : 16)) blend_
             const int c0 = c * 32;
             uint32_t bits = __ballot_sync(0xffffffffu, c0 + lane < cnt && (s_mask[c0 + lane] & my_bit));
             uint32_t pass = 0;
+            // two entries per step (the second repeats the first when only
+            // one is left): half the loop overhead, two independent chains
             while (bits) {
                 const int j = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const int j2 = bits ? __ffs(bits) - 1 : j;
                 bits &= bits - 1u;
                 if (done) continue;
                 const float4 g0 = s_g0[c0 + j];
                 const float4 g1 = s_g1[c0 + j];
-                const float dx = pxf - g0.x;
-                const float dy = pyf - g0.y;
-                const float e = g0.w * dy;
-                const float f = (g1.x * dy) * dy;
-                const float q = fmaf(dx, fmaf(g0.z, dx, e), f);
-                if (kStats) ++n_exec;
+                const float4 h0 = s_g0[c0 + j2];
+                const float4 h1 = s_g1[c0 + j2];
+                const float dx = pxf - g0.x, dy = pyf - g0.y;
+                const float ex = pxf - h0.x, ey = pyf - h0.y;
+                const float q = fmaf(dx, fmaf(g0.z, dx, g0.w * dy), (g1.x * dy) * dy);
+                const float q2 = fmaf(ex, fmaf(h0.z, ex, h0.w * ey), (h1.x * ey) * ey);
+                if (kStats) n_exec += (j2 != j) ? 2u : 1u;
                 if (q <= g1.y) pass |= 1u << j;
+                if (q2 <= h1.y) pass |= 1u << j2;
             }
             s_pass[warp][c][lane] = pass;
         }
