@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--mv-cams", type=int, default=64)
     p.add_argument("--mv-n", type=int, default=1_500_000)
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-backward", action="store_true")
     p.add_argument("--serve-duration", type=float, default=1.5, help="seconds of arrivals per rate")
     p.add_argument("--serve-rates", default="200,500,1000,2000")
     return p.parse_args()
@@ -478,6 +479,12 @@ def run_ours(args):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "path": "pinned host scene -> device copy, gs_forward, image -> pinned host, per frame"}
 
+    # --- backward of the same frame: render backward, preprocess backward and
+    # the pruning score, alone and after its forward
+    backward = None
+    if not args.no_backward:
+        backward = run_backward(args, raster, rast, scene, cam, cfg_acc, f_acc, stream, max_over_ranks, barrier)
+
     # --- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -515,9 +522,51 @@ def run_ours(args):
               "speedup_vs_3sigma": (per_mode["3sigma"]["ms_per_frame"] / ms_acc) if "3sigma" in per_mode else None,
               "stages_ms": stages, "stage_roofline": stage_frac,
               "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
-              "cpu_baseline": cpu, "multiview": multiview, "served": served})
+              "cpu_baseline": cpu, "backward": backward, "multiview": multiview, "served": served})
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_backward(args, raster, rast, scene, cam, cfg, frame, stream, max_over_ranks, barrier):
+    """gs_render_backward on the headline frame: dL/dimage ~ N(0, 1), all
+    parameter gradients, the 2D-mean gradient and the pruning score."""
+    import torch
+
+    n = int(scene.means.shape[1])
+    dev = scene.means.device
+    grads = {k: torch.empty_like(getattr(scene, k)) for k in ("means", "scales", "rotations", "opacities", "sh")}
+    grads["means2d"] = torch.empty(2, n, dtype=torch.float32, device=dev)
+    grads["score"] = torch.zeros(n, dtype=torch.float32, device=dev)
+    work = torch.empty(raster.backward_work_bytes(n) // 4, dtype=torch.float32, device=dev)
+    gen = torch.Generator(device=dev).manual_seed(7)
+    dL = torch.randn(3, cam.height, cam.width, device=dev, generator=gen)
+    steps = min(args.steps, 50)
+
+    def timed_loop(fn):
+        for _ in range(3):
+            fn()
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(steps):
+            fn()
+        a1.record(stream)
+        barrier()
+        return max_over_ranks(a0.elapsed_time(a1)) / steps
+
+    rast.gs_forward(scene, cam, cfg, frame)  # the frame the backward walks
+    ms_b = timed_loop(lambda: rast.gs_render_backward(scene, cam, cfg, frame, dL, grads, work))
+
+    def step():
+        rast.gs_forward(scene, cam, cfg, frame)
+        rast.gs_render_backward(scene, cam, cfg, frame, dL, grads, work)
+
+    ms_fb = timed_loop(step)
+    return {"workload": f"{WORKLOAD} AccuTile frame, dL/dimage ~ N(0, 1)", "steps": steps,
+            "ms_backward": ms_b, "ms_forward_plus_backward": ms_fb,
+            "kernels": "memset, blend_backward<16>, preprocess_backward",
+            "gaussians_with_score": int((grads["score"] > 0).sum().item())}
 
 
 def run_multiview(args, dev, max_over_ranks, barrier):
