@@ -211,7 +211,8 @@ gs_status gs_forward(gs_context* ctx, const gs_scene* scene, const gs_camera* ca
  *   score [n] (nullable): the efficient pruning score of Sec. 4.2.1,
  *   sum over pixels and channels of (dC/dg_i)^2, is ADDED to it so views can
  *   be accumulated,
- *   work: library scratch of gs_backward_work_bytes(n_capacity) bytes. */
+ *   work: library scratch of gs_backward_work_bytes(n_capacity) bytes,
+ *   16-byte aligned (GS_ERR_INVALID otherwise). */
 typedef struct gs_grads {
     float* means;
     float* scales;

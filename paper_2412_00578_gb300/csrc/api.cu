@@ -291,6 +291,8 @@ gs_status gs_render_backward(gs_context* ctx, const gs_scene* scene, const gs_ca
         return set_error(ctx, GS_ERR_INVALID, "scene is NULL or larger than the frame");
     if (!dL_dimage || !grads || !grads->work)
         return set_error(ctx, GS_ERR_INVALID, "dL_dimage, grads or grads->work is NULL");
+    if (reinterpret_cast<uintptr_t>(grads->work) & 15)
+        return set_error(ctx, GS_ERR_INVALID, "grads->work must be 16-byte aligned");
     if (scene->n > 0 && (!scene->means || !scene->scales || !scene->rotations || !scene->sh || !grads->means ||
                          !grads->scales || !grads->rotations || !grads->opacities || !grads->sh))
         return set_error(ctx, GS_ERR_INVALID, "scene or grads has a NULL array");

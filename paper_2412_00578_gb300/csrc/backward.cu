@@ -12,8 +12,9 @@
 //   unclamped alpha = sigma g: dL/dsigma = dL/dalpha g,
 //   dL/dq = -dL/dalpha sigma g / 2, q = a dx^2 + 2 b dx dy + c dy^2,
 //   score += sum_ch (sigma T (c_ch - B_ch))^2   (dC/dg squared).
-// The warp sums its lanes' ten values per Gaussian (butterfly shuffles)
-// before one atomic add per value into the per-Gaussian work array.
+// The warp sums its lanes' ten values per Gaussian (halving shuffle
+// exchanges) and adds them with three vector atomics into the Gaussian's
+// 12-float row of the work array.
 //
 // preprocess_backward: one thread per Gaussian, carries the 2D sums to
 // mu, s, q, h, sigma through the conic inverse, Sigma2D = J W Sigma3D W^T J^T
@@ -24,13 +25,8 @@
 namespace gs {
 namespace {
 
-constexpr int kWork = 10;  // du dv da db dc dsigma dr dg db score
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
+constexpr int kWork = 10;     // du dv da db dc dsigma dr dg db score
+constexpr int kWorkRow = 12;  // floats per Gaussian row of the work array (three 16-byte groups)
 
 struct BwdArgs {
     const uint2* ranges;
@@ -41,7 +37,7 @@ struct BwdArgs {
     const float* final_T;
     const uint32_t* last;
     const float* dL_dimg;  // [3][H][W]
-    float* work;           // [kWork][ncap]
+    float* work;           // [ncap][kWorkRow], row = the kWork values and 2 pad
     int64_t ncap;
     int width, height, gx;
     float bg0, bg1, bg2;
@@ -155,12 +151,37 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_
                     }
                 }
                 if (__any_sync(0xffffffffu, has)) {
-                    const uint32_t id = s_id[k];
+                    // Warp sum of the 10 values by halving exchanges: after
+                    // the steps over lane bits 4 and 3 each lane keeps 4 of 16
+                    // (zero-padded) values, group lane >> 3; three more steps
+                    // complete the sums.  Lanes 0, 8 and 16 then add groups
+                    // 0..3, 4..7 and 8..9 to the Gaussian's row with one vector
+                    // atomic each.
+                    float w[16];
 #pragma unroll
-                    for (int m = 0; m < kWork; ++m) {
-                        const float sum = warp_sum(has ? v[m] : 0.0f);
-                        if (lane == m) atomicAdd(A.work + (size_t)m * A.ncap + id, sum);
+                    for (int m = 0; m < 16; ++m) w[m] = (m < kWork && has) ? v[m < kWork ? m : 0] : 0.0f;
+                    const bool up16 = (lane & 16) != 0;
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        const float send = up16 ? w[m] : w[m + 8];
+                        const float keep = up16 ? w[m + 8] : w[m];
+                        w[m] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
                     }
+                    const bool up8 = (lane & 8) != 0;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const float send = up8 ? w[m] : w[m + 4];
+                        const float keep = up8 ? w[m + 4] : w[m];
+                        w[m] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+                    }
+#pragma unroll
+                    for (int off = 4; off > 0; off >>= 1)
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) w[m] += __shfl_xor_sync(0xffffffffu, w[m], off);
+                    float* row = A.work + (size_t)s_id[k] * kWorkRow;
+                    if (lane == 0) atomicAdd(reinterpret_cast<float4*>(row), make_float4(w[0], w[1], w[2], w[3]));
+                    else if (lane == 8) atomicAdd(reinterpret_cast<float4*>(row + 4), make_float4(w[0], w[1], w[2], w[3]));
+                    else if (lane == 16) atomicAdd(reinterpret_cast<float2*>(row + 8), make_float2(w[0], w[1]));
                 }
             }
         }
@@ -242,10 +263,17 @@ __device__ void sh_eval(float x, float y, float z, float Y[16], float dY[16][3])
 __global__ void __launch_bounds__(256) preprocess_backward_kernel(const PreBwdArgs A) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
-    const int64_t n = A.n, nc = A.ncap;
+    const int64_t n = A.n;
     float gr[kWork];
-#pragma unroll
-    for (int m = 0; m < kWork; ++m) gr[m] = A.work[(size_t)m * nc + i];
+    {
+        const float* row = A.work + (size_t)i * kWorkRow;
+        const float4 a = *reinterpret_cast<const float4*>(row);
+        const float4 b = *reinterpret_cast<const float4*>(row + 4);
+        const float2 c = *reinterpret_cast<const float2*>(row + 8);
+        gr[0] = a.x, gr[1] = a.y, gr[2] = a.z, gr[3] = a.w;
+        gr[4] = b.x, gr[5] = b.y, gr[6] = b.z, gr[7] = b.w;
+        gr[8] = c.x, gr[9] = c.y;
+    }
     if (A.score) A.score[i] += gr[9];
     if (A.g_means2d) {
         A.g_means2d[i] = gr[0];
@@ -395,7 +423,7 @@ __global__ void __launch_bounds__(256) preprocess_backward_kernel(const PreBwdAr
 
 }  // namespace
 
-int64_t backward_work_floats(int64_t ncap) { return (int64_t)kWork * ncap; }
+int64_t backward_work_floats(int64_t ncap) { return (int64_t)kWorkRow * ncap; }
 
 gs_status launch_backward(gs_context* ctx, const gs_scene* s, const gs_camera* cam, const gs_raster_cfg* cfg,
                           const FrameView& v, const float* dL_dimg, const gs_grads* g) {
