@@ -197,6 +197,9 @@ gs_status launch_preprocess(gs_context* ctx, const gs_scene* s, const gs_camera*
 gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v);
 gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override = 0);
 gs_status launch_ranges(gs_context* ctx, const FrameView& v);
+// Heaviest-first launch order of the tiles (kept in the idle sort look-back
+// table), or nullptr when the tiles do not fit it (then CTA = tile).
+const uint32_t* launch_tile_order(gs_context* ctx, const FrameView& v);
 gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v,
                         unsigned long long* stats = nullptr);
 gs_status launch_backward(gs_context* ctx, const gs_scene* s, const gs_camera* cam, const gs_raster_cfg* cfg,

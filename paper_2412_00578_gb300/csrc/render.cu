@@ -346,6 +346,16 @@ gs_status launch_ranges(gs_context* ctx, const FrameView& v) {
     return check_launch(ctx, "tile_ranges");
 }
 
+const uint32_t* launch_tile_order(gs_context* ctx, const FrameView& v) {
+    // The order array lives in the sort's look-back table, idle until the next
+    // sort, which clears every word of it that it reads before reading it.
+    const unsigned tiles = (unsigned)(v.gx * v.gy);
+    if (tiles == 0 || tiles > kMaxOrderedTiles || (int64_t)tiles > 2 * v.sort_partitions * 256) return nullptr;
+    tile_order_kernel<<<1, 1024, 0, ctx->stream>>>(v.ranges, tiles, v.sort_lookback);
+    ctx->launches += 1;
+    return v.sort_lookback;
+}
+
 gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v, unsigned long long* stats) {
     BlendArgs A;
     A.ranges = v.ranges;
@@ -369,14 +379,7 @@ gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameVi
     A.pixel_capacity = v.pixel_capacity;
     const unsigned tiles = (unsigned)(v.gx * v.gy);
     if (tiles == 0) return GS_OK;
-    // The order array lives in the sort's look-back table, idle until the next
-    // sort, which clears every word of it that it reads before reading it.
-    A.order = nullptr;
-    if (tiles <= kMaxOrderedTiles && (int64_t)tiles <= 2 * v.sort_partitions * 256) {
-        tile_order_kernel<<<1, 1024, 0, ctx->stream>>>(v.ranges, tiles, v.sort_lookback);
-        ctx->launches += 1;
-        A.order = v.sort_lookback;
-    }
+    A.order = launch_tile_order(ctx, v);
 #define GS_BLEND_LAUNCH(T_, S_, M_) blend_kernel<T_, S_, M_><<<tiles, T_ * T_, 0, ctx->stream>>>(A)
 #define GS_BLEND_TILES(S_, M_)                                                             \
     switch (v.tile) {                                                                      \
