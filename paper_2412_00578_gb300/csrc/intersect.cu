@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const int32_t
 }
 
 __global__ void __launch_bounds__(1024) scan_top_kernel(long long* __restrict__ partials, int64_t nblocks,
-                                                        int64_t kcap, uint32_t* __restrict__ status) {
+                                                        int64_t kcap, uint32_t* __restrict__ status, bool clear3) {
     __shared__ long long s_warp[32];
     __shared__ long long s_carry;
     if (threadIdx.x == 0) s_carry = 0;
@@ -85,9 +85,12 @@ __global__ void __launch_bounds__(1024) scan_top_kernel(long long* __restrict__ 
     }
     if (threadIdx.x == 0) {
         const long long K = s_carry;
+        // words 0..2 (and 3 for a single camera; a batch's set-up kernel has
+        // just written its word 3) start this frame's status afresh
         status[0] = (uint32_t)(K & 0xffffffffll);
         status[1] = (uint32_t)(K >> 32);
-        if (K > kcap) atomicOr(status + 2, GS_FLAG_CAPACITY);
+        status[2] = K > kcap ? GS_FLAG_CAPACITY : 0u;
+        if (clear3) status[3] = 0u;
     }
 }
 
@@ -219,15 +222,11 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
 
 gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v) {
     const int64_t nb = scan_blocks_for(v.ncap);
-    // clear the key total and flags: words 0..2, and word 3 too for a single
-    // camera (a batch's set-up kernel has just written its word 3)
-    if (cudaMemsetAsync(v.status, 0, (v.table ? 3 : 4) * sizeof(uint32_t), ctx->stream) != cudaSuccess)
-        return set_error(ctx, GS_ERR_CUDA, "intersect: cudaMemsetAsync(status) failed");
     if (nb > 0) {
         scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(v.counts, v.ncap, v.scan_partials);
         ctx->launches += 1;
     }
-    scan_top_kernel<<<1, 1024, 0, ctx->stream>>>(v.scan_partials, nb, v.kcap, v.status);
+    scan_top_kernel<<<1, 1024, 0, ctx->stream>>>(v.scan_partials, nb, v.kcap, v.status, v.table == nullptr);
     ctx->launches += 1;
     if (nb > 0) {
         EmitArgs A;
