@@ -291,17 +291,43 @@ def test_outdoor_3m_1280x840_full_frame(raster, outdoor, mode):
     benchmark times (gs_forward, tile 16): every key, range and pixel."""
     scene, cam = outdoor
     r = raster.Renderer("cuda:0")
-    out = r.render(scene.to("cuda:0"), cam, mode=mode, tile=16)
-    torch.cuda.synchronize()
+    ds = scene.to("cuda:0")
+    out = r.render(ds, cam, mode=mode, tile=16)  # sizes the frame (stage calls)
+    f = out.frame
+    f.image.fill_(-1.0)
+    f.keys.fill_(-1)
+    r.rast.gs_forward(ds, cam, raster.cfg_struct(16, mode), f)  # the call the benchmark times
+    K, flags = r.rast.gs_read_status(f)
     ref = oracle.render(scene, cam, 16, mode, prec64=False)
+    assert K == ref["num_keys"] and flags == 0
+    assert np.array_equal(f.keys[:K].cpu().numpy().view(np.uint64), ref["keys"])
+    assert np.array_equal(f.vals[:K].cpu().numpy().view(np.uint32), ref["vals"])
+    assert np.array_equal(f.tile_ranges().cpu().numpy().view(np.uint32), ref["ranges"])
+    err = np.abs(f.image.cpu().numpy().astype(np.float64) - ref["image"]).max()
+    assert err <= IMG_TOL, err
+    assert np.array_equal(f.last.cpu().numpy().view(np.uint32), ref["last"])
+    print(f"outdoor 3M mode {mode}: K={K}, image max abs err {err:.3g}")
+
+
+def test_4k_tile8_many_tiles():
+    """3840x2160 at tile 8: 129,600 tiles, so 49-bit keys (an eight-pass sort of
+    7-bit digits) and more tiles than the blend's launch-order table holds
+    (tiles then run in index order); 400k blob Gaussians through the stage calls."""
+    from paper_2412_00578_gb300 import raster
+
+    scene = synth.blob_scene(400_000, seed=9)
+    cam = synth.pinhole(3840, 2160, 60.0, np.eye(3), np.array([0.0, 0.0, 25.0]))
+    ref = oracle.render(scene, cam, 8, 2, prec64=False)
+    r = raster.Renderer("cuda:0")
+    out = r.render(scene.to("cuda:0"), cam, mode="accutile", tile=8)
+    torch.cuda.synchronize()
     K = out.num_keys
-    assert K == ref["num_keys"]
+    assert K == ref["num_keys"] and ref["grid"][0] * ref["grid"][1] == 129_600
     assert np.array_equal(out.frame.keys[:K].cpu().numpy().view(np.uint64), ref["keys"])
     assert np.array_equal(out.frame.vals[:K].cpu().numpy().view(np.uint32), ref["vals"])
     assert np.array_equal(out.frame.tile_ranges().cpu().numpy().view(np.uint32), ref["ranges"])
-    err = np.abs(out.image.cpu().numpy().astype(np.float64) - ref["image"]).max()
-    assert err <= IMG_TOL, err
-    print(f"outdoor 3M mode {mode}: K={K}, image max abs err {err:.3g}")
+    assert np.abs(out.image.cpu().numpy().astype(np.float64) - ref["image"]).max() <= IMG_TOL
+    assert np.array_equal(out.last.cpu().numpy().view(np.uint32), ref["last"])
 
 
 def test_outdoor_pruned_300k(raster, outdoor):
