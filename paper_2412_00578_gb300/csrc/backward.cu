@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_
                         const float g = gs_expf_blend(-0.5f * q);
                         const float raw = g1.z * g;
                         const float alpha = fminf(0.99f, raw);
-                        const float Tb = Tr / (1.0f - alpha);
+                        const float Tb = __fdividef(Tr, 1.0f - alpha);
                         const float4 col = s_g2[k];
                         const float w = alpha * Tb;
                         v[6] = G0 * w;
@@ -150,7 +150,16 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_
                         Tr = Tb;
                     }
                 }
-                if (__any_sync(0xffffffffu, has)) {
+                const uint32_t hm = __ballot_sync(0xffffffffu, has);
+                if (hm != 0u && __popc(hm) <= 2) {
+                    // one or two pixels took this Gaussian: each adds its own values
+                    if (has) {
+                        float* row = A.work + (size_t)s_id[k] * kWorkRow;
+                        atomicAdd(reinterpret_cast<float4*>(row), make_float4(v[0], v[1], v[2], v[3]));
+                        atomicAdd(reinterpret_cast<float4*>(row + 4), make_float4(v[4], v[5], v[6], v[7]));
+                        atomicAdd(reinterpret_cast<float2*>(row + 8), make_float2(v[8], v[9]));
+                    }
+                } else if (hm != 0u) {
                     // Warp sum of the 10 values by halving exchanges: after
                     // the steps over lane bits 4 and 3 each lane keeps 4 of 16
                     // (zero-padded) values, group lane >> 3; three more steps
