@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_
                     }
                 }
                 const uint32_t hm = __ballot_sync(0xffffffffu, has);
-                if (hm != 0u && __popc(hm) <= 8) {
+                if (hm != 0u && __popc(hm) <= 16) {
                     // up to eight pixels took this Gaussian: each adds its own values
                     if (has) {
                         float* row = A.work + (size_t)s_id[k] * kWorkRow;
