@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_
                 }
                 const uint32_t hm = __ballot_sync(0xffffffffu, has);
                 if (hm != 0u && __popc(hm) <= 16) {
-                    // up to eight pixels took this Gaussian: each adds its own values
+                    // up to sixteen pixels took this Gaussian: each adds its own values (cheaper
+                    // than the warp reduction below at these counts)
                     if (has) {
                         float* row = A.work + (size_t)s_id[k] * kWorkRow;
                         atomicAdd(reinterpret_cast<float4*>(row), make_float4(v[0], v[1], v[2], v[3]));
