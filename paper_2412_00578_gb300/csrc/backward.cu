@@ -270,7 +270,7 @@ __device__ void sh_eval(float x, float y, float z, float Y[16], float dY[16][3])
         for (int j = 0; j < 3; ++j) dY[k][j] = g[k][j];
 }
 
-__global__ void __launch_bounds__(256) preprocess_backward_kernel(const PreBwdArgs A) {
+__global__ void __launch_bounds__(256, 4) preprocess_backward_kernel(const PreBwdArgs A) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
     const int64_t n = A.n;
