@@ -69,7 +69,7 @@ def _declare(L):
     L.oracle_snugbox.restype = I32
     L.oracle_exact_tile_mask.argtypes = [P, I32, I32, I32, P]
     L.oracle_render.argtypes = [I32, I64, P, P, P, P, P, I32, I32, I32, P, I32, I32, P, I64, P, P, P, P, P, P, P, P,
-                                P]
+                                P, P]
     L.oracle_render.restype = I32
     L.oracle_render_notile.argtypes = [I32, I64, P, P, P, P, P, I32, I32, I32, P, P, P, P, I32, P]
     L.oracle_blend_pixel.argtypes = [I32, P, I64, ctypes.c_double, ctypes.c_double, P, P]
@@ -175,7 +175,9 @@ def count_keys(scene, cam, tile: int, mode: int, prec64: bool = False) -> int:
 def render(scene, cam, tile: int = 16, mode: int = 2, bg=(0.0, 0.0, 0.0), prec64: bool = False, key_cap=None):
     """Full forward pipeline of one tile mode.  Returns a dict with the
     unsorted and sorted (key, id) lists, tile ranges, image (3,H,W), final T
-    and last-contributor index, all as numpy arrays."""
+    and last-contributor index, all as numpy arrays, and the blend's pair
+    counts (evaluated: every tile-list entry a pixel walks, up to and
+    including the one that stops it; contributing: those that add colour)."""
     n, (m, s, r, o, sh), deg = _scene_arrays(scene)
     w, h, cf = _cam(cam)
     gx, gy = grid(w, h, tile)
@@ -192,13 +194,15 @@ def render(scene, cam, tile: int = 16, mode: int = 2, bg=(0.0, 0.0, 0.0), prec64
     img = np.zeros((3, h, w), np.float64)
     T = np.zeros((h, w), np.float64)
     last = np.zeros((h, w), np.uint32)
+    pairs = np.zeros(2, np.int64)
     rc = lib().oracle_render(int(prec64), n, _ptr(m), _ptr(s), _ptr(r), _ptr(o), _ptr(sh), deg, w, h, _ptr(cf), tile,
                              mode, _ptr(bgv), key_cap, _ptr(ku), _ptr(vu), _ptr(ks), _ptr(vs), _ptr(nk),
-                             _ptr(ranges), _ptr(img), _ptr(T), _ptr(last))
+                             _ptr(ranges), _ptr(img), _ptr(T), _ptr(last), _ptr(pairs))
     K = int(nk[0])
     if rc != 0:
         raise RuntimeError(f"oracle_render: key capacity {key_cap} < required {K}")
-    return {"num_keys": K, "keys_unsorted": ku[:K], "vals_unsorted": vu[:K], "keys": ks[:K], "vals": vs[:K],
+    return {"num_keys": K, "evaluated_pairs": int(pairs[0]), "contributing_pairs": int(pairs[1]),
+            "keys_unsorted": ku[:K], "vals_unsorted": vu[:K], "keys": ks[:K], "vals": vs[:K],
             "ranges": ranges, "image": img, "final_T": T, "last": last, "grid": (gx, gy)}
 
 

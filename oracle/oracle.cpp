@@ -534,6 +534,7 @@ template <typename R> struct Pixel {
     R C[3] = {0, 0, 0};
     R T = R(1);
     uint32_t last = 0;
+    uint32_t contributed = 0;  // Gaussians that added to C
 };
 
 template <typename R>
@@ -553,6 +554,7 @@ bool blend_step(Pixel<R>& px, const Proj<R>& P, R pxf, R pyf, uint32_t pos) {
     for (int ch = 0; ch < 3; ++ch) px.C[ch] = std::fma(P.rgb[ch], w, px.C[ch]);
     px.T = Tn;
     px.last = pos;
+    px.contributed += 1;
     return true;
 }
 
@@ -575,7 +577,7 @@ template <typename R>
 int render_impl(const SceneIn& s, int width, int height, const float* camf, int tile, int mode, const float* bg,
                 int64_t key_cap, uint64_t* keys_unsorted, uint32_t* vals_unsorted, uint64_t* keys_sorted,
                 uint32_t* vals_sorted, int64_t* num_keys, uint32_t* ranges, double* image, double* final_T,
-                uint32_t* last) {
+                uint32_t* last, int64_t* pair_counts) {
     Cam<R> cam = make_cam<R>(width, height, camf);
     Grid g = make_grid(width, height, tile);
     std::vector<Proj<R>> P = preprocess_all<R>(s, cam);
@@ -616,21 +618,34 @@ int render_impl(const SceneIn& s, int width, int height, const float* camf, int 
         if (k == 0 || static_cast<uint32_t>(keys_sorted[k - 1] >> 32) != tid) ranges[2 * tid] = uint32_t(k);
         if (k == K - 1 || static_cast<uint32_t>(keys_sorted[k + 1] >> 32) != tid) ranges[2 * tid + 1] = uint32_t(k + 1);
     }
-    // render: each pixel walks its tile's list front to back.
+    // render: each pixel walks its tile's list front to back.  pair_counts
+    // (nullable) receives the pairs the walk evaluates (every entry up to and
+    // including the one that stops the pixel) and the pairs that add colour.
     const int64_t HW = int64_t(width) * height;
+    int64_t evaluated = 0, contributed = 0;
     for (int py = 0; py < height; ++py) {
         for (int px = 0; px < width; ++px) {
             int64_t tid = int64_t(py / tile) * g.gx + (px / tile);
             uint32_t start = ranges[2 * tid], end = ranges[2 * tid + 1];
             Pixel<R> pix;
-            for (uint32_t k = start; k < end; ++k) {
-                if (!blend_step<R>(pix, P[vals_sorted[k]], R(px), R(py), k - start + 1)) break;
+            uint32_t k = start;
+            for (; k < end; ++k) {
+                if (!blend_step<R>(pix, P[vals_sorted[k]], R(px), R(py), k - start + 1)) {
+                    ++k;  // the stopping entry was evaluated too
+                    break;
+                }
             }
+            evaluated += k - start;
+            contributed += pix.contributed;
             int64_t o = int64_t(py) * width + px;
             for (int ch = 0; ch < 3; ++ch) image[ch * HW + o] = double(std::fma(pix.T, R(bg[ch]), pix.C[ch]));
             final_T[o] = double(pix.T);
             last[o] = pix.last;
         }
+    }
+    if (pair_counts) {
+        pair_counts[0] = evaluated;
+        pair_counts[1] = contributed;
     }
     return 0;
 }
@@ -1042,13 +1057,13 @@ int oracle_render(int prec64, int64_t n, const float* means, const float* scales
                   const float* opac, const float* sh, int sh_degree, int width, int height, const float* camf,
                   int tile, int mode, const float* bg, int64_t key_cap, uint64_t* keys_unsorted,
                   uint32_t* vals_unsorted, uint64_t* keys_sorted, uint32_t* vals_sorted, int64_t* num_keys,
-                  uint32_t* ranges, double* image, double* final_T, uint32_t* last) {
+                  uint32_t* ranges, double* image, double* final_T, uint32_t* last, int64_t* pair_counts) {
     SceneIn s{n, sh_degree, means, scales, rots, opac, sh};
     if (prec64)
         return render_impl<double>(s, width, height, camf, tile, mode, bg, key_cap, keys_unsorted, vals_unsorted,
-                                   keys_sorted, vals_sorted, num_keys, ranges, image, final_T, last);
+                                   keys_sorted, vals_sorted, num_keys, ranges, image, final_T, last, pair_counts);
     return render_impl<float>(s, width, height, camf, tile, mode, bg, key_cap, keys_unsorted, vals_unsorted,
-                              keys_sorted, vals_sorted, num_keys, ranges, image, final_T, last);
+                              keys_sorted, vals_sorted, num_keys, ranges, image, final_T, last, pair_counts);
 }
 
 void oracle_render_notile(int prec64, int64_t n, const float* means, const float* scales, const float* rots,

@@ -120,6 +120,19 @@ def test_ragged_small(raster, rast, mode, tile):
     check_against_oracle(gpu, scene, cam, mode, tile, bg=(0.1, 0.2, 0.3))
 
 
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_render_stats_pair_counts(raster, rast, tile):
+    """gs_render_stats: the evaluated and contributing pair counts (the blend
+    work the benchmark's roofline divides by time) equal the oracle's walk;
+    the pairs the kernel tested after its culling lie between the two."""
+    for scene, cam in [ragged_case(), synth.small_box_workload()]:
+        gpu = run_pipeline(raster, rast, scene, cam, 2, tile)
+        ev, co, ex = rast.gs_render_stats(cam, raster.cfg_struct(tile, 2), gpu["frame"])
+        ref = oracle.render(scene, cam, tile, 2, prec64=False)
+        assert ev == ref["evaluated_pairs"] and co == ref["contributing_pairs"]
+        assert co <= ex <= ev
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_box_16k_320x240(raster, rast, mode):
     scene, cam = synth.small_box_workload()

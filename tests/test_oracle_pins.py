@@ -428,3 +428,32 @@ def test_key_counts_decrease_with_precision_of_mode():
     scene, cam = synth.small_box_workload()
     k = [oracle.count_keys(scene, cam, 16, m) for m in (SIG3, SNUG, ACCU)]
     assert k[0] > k[1] > k[2] > 0
+
+
+def test_blend_pair_counts():
+    """The blend's pair counts (the work the roofline counts).  Faint splats
+    never stop a pixel, so every pixel evaluates its whole tile list: the
+    evaluated pairs equal the sum over tiles of entries x pixels of the tile
+    inside the image.  AccuTile and SnugBox give the same images, hence the
+    same contributing pairs, and SnugBox's lists are supersets of AccuTile's."""
+    scene = synth.uniform_box_scene(2500, seed=71, log_scale_mu=-3.0)
+    cam = synth.pinhole(97, 61, 60.0, np.eye(3), np.array([0.0, 0.0, 5.0]))
+    faint = synth.uniform_box_scene(2500, seed=71, log_scale_mu=-3.0)
+    faint.opacities[:] = 0.01
+    for tile in (8, 16):
+        r = oracle.render(faint, cam, tile, 2, prec64=False)
+        gx, gy = r["grid"]
+        rng = r["ranges"].reshape(-1, 2).astype(np.int64)
+        n = rng[:, 1] - rng[:, 0]
+        tx, ty = np.arange(gx * gy) % gx, np.arange(gx * gy) // gx
+        pw = np.minimum(tile, cam.width - tx * tile)
+        ph = np.minimum(tile, cam.height - ty * tile)
+        assert np.all(r["final_T"] >= 1e-4)  # precondition: nothing stopped
+        assert r["evaluated_pairs"] == int((n * pw * ph).sum())
+        assert 0 < r["contributing_pairs"] < r["evaluated_pairs"]
+    acc = oracle.render(scene, cam, 16, 2, prec64=False)
+    snug = oracle.render(scene, cam, 16, 1, prec64=False)
+    assert np.array_equal(acc["image"], snug["image"])
+    assert acc["contributing_pairs"] == snug["contributing_pairs"]
+    assert snug["evaluated_pairs"] >= acc["evaluated_pairs"]
+    assert acc["evaluated_pairs"] > acc["contributing_pairs"] > 0
