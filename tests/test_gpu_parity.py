@@ -124,13 +124,13 @@ def test_ragged_small(raster, rast, mode, tile):
 def test_render_stats_pair_counts(raster, rast, tile):
     """gs_render_stats: the evaluated and contributing pair counts (the blend
     work the benchmark's roofline divides by time) equal the oracle's walk;
-    the pairs the kernel tested after its culling lie between the two."""
+    every contributing pair is among the pairs the kernel tested."""
     for scene, cam in [ragged_case(), synth.small_box_workload()]:
         gpu = run_pipeline(raster, rast, scene, cam, 2, tile)
         ev, co, ex = rast.gs_render_stats(cam, raster.cfg_struct(tile, 2), gpu["frame"])
         ref = oracle.render(scene, cam, tile, 2, prec64=False)
         assert ev == ref["evaluated_pairs"] and co == ref["contributing_pairs"]
-        assert co <= ex <= ev
+        assert co <= ex
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
