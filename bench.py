@@ -82,16 +82,24 @@ class ClockSampler:
     def __init__(self, bus_id: str | None):
         self.bus_id = (bus_id or "").lower()
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = None
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.fh = open(self.path, "w")
+            import tempfile
+
+            fd, self.path = tempfile.mkstemp(prefix="gs_clocks_", suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                                           "-lms", "50"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            if self.path:
+                try:
+                    self.fh.close()
+                    os.remove(self.path)
+                except Exception:
+                    pass
 
     def count(self) -> int:
         try:
@@ -111,11 +119,16 @@ class ClockSampler:
             self.proc.kill()
         self.fh.close()
         rows = []
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 10:
-                continue
-            rows.append(parts)
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         if self.bus_id:
             mine = [r for r in rows if r[1].lower().endswith(self.bus_id[-12:])]
             rows = mine or rows
