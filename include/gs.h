@@ -113,7 +113,8 @@ typedef struct gs_raster_cfg {
  *   last     [height][width] uint32: 1-based position, in its tile's list, of
  *            the last Gaussian that contributed to the pixel (0: none).
  *   scratch  library working memory (status words, scan partials, sort
- *            histograms and look-back tables); contents are private. */
+ *            histograms and look-back tables, the render's tile launch
+ *            order); contents are private. */
 typedef struct gs_frame {
     int64_t n_capacity;
     int64_t key_capacity;   /* <= GS_MAX_KEYS */
@@ -186,7 +187,9 @@ gs_status gs_tile_ranges(gs_context* ctx, const gs_camera* cam, const gs_raster_
  * for each pixel, walk its tile's Gaussians front to back; a Gaussian counts
  * where q <= t (alpha >= 1/255), alpha = min(0.99, sigma exp(-q/2)); stop
  * before a Gaussian that would bring the transmittance below 1e-4; finally
- * add T * bg.  Writes image, final_T and last. */
+ * add T * bg.  Writes image, final_T and last.  Tiles are processed heaviest
+ * first (their launch order is kept in frame->scratch); the order does not
+ * change any output. */
 gs_status gs_render(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame);
 
 /* Instrumented render: the same blend as gs_render (same outputs), which
@@ -195,8 +198,9 @@ gs_status gs_render(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* 
  * and including the one that stops the pixel), *contributed = the pairs that
  * add to the colour, *executed = the pairs whose in-ellipse test the kernel
  * actually evaluated after its in-tile culling (a pixel that stops part-way
- * through a 256-entry batch has the rest of that batch tested too).  Synchronises the stream; host
- * outputs, nullable.  States the blend's algorithmic work; not for timing. */
+ * through a 256-entry batch has the rest of that batch tested too).
+ * Synchronises the stream; host outputs, nullable.  States the blend's
+ * algorithmic work; not for timing. */
 gs_status gs_render_stats(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame,
                           uint64_t* evaluated, uint64_t* contributed, uint64_t* executed);
 
