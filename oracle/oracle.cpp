@@ -210,8 +210,11 @@ template <typename R> Proj<R> preprocess_one(const SceneIn& s, int64_t i, const 
     if (!(p[2] > cam.near_z)) return P;
 
     // Perspective projection of the mean (pixel (i, j) at point (i, j)).
-    R xz = p[0] / p[2];
-    R yz = p[1] / p[2];
+    // Reading: quotients by one denominator are products with its reciprocal
+    // (1/z here; 1/|q|, 1/det and 1/|mu - campos| below).
+    R iz = R(1) / p[2];
+    R xz = p[0] * iz;
+    R yz = p[1] * iz;
     R u = cam.fx * xz + cam.cx;
     R v = cam.fy * yz + cam.cy;
 
@@ -219,7 +222,8 @@ template <typename R> Proj<R> preprocess_one(const SceneIn& s, int64_t i, const 
     R n2 = ((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3];
     if (!(n2 > R(0))) return P;
     R nq = std::sqrt(n2);
-    R w = q[0] / nq, x = q[1] / nq, y = q[2] / nq, z = q[3] / nq;
+    R inq = R(1) / nq;
+    R w = q[0] * inq, x = q[1] * inq, y = q[2] * inq, z = q[3] * inq;
     R Rm[3][3];
     Rm[0][0] = R(1) - R(2) * (y * y + z * z);
     Rm[0][1] = R(2) * (x * y - w * z);
@@ -246,11 +250,11 @@ template <typename R> Proj<R> preprocess_one(const SceneIn& s, int64_t i, const 
     R limy = R(1.3) * cam.tan_fovy;
     R tx = std::min(limx, std::max(-limx, xz)) * p[2];
     R ty = std::min(limy, std::max(-limy, yz)) * p[2];
-    R zz = p[2] * p[2];
-    R j00 = cam.fx / p[2];
-    R j02 = -((cam.fx * tx) / zz);
-    R j11 = cam.fy / p[2];
-    R j12 = -((cam.fy * ty) / zz);
+    R iz2 = iz * iz;
+    R j00 = cam.fx * iz;
+    R j02 = -((cam.fx * tx) * iz2);
+    R j11 = cam.fy * iz;
+    R j12 = -((cam.fy * ty) * iz2);
 
     // T = J W (2x3); the zero entries of J contribute nothing.
     R T[2][3];
@@ -273,9 +277,10 @@ template <typename R> Proj<R> preprocess_one(const SceneIn& s, int64_t i, const 
     R sxy = s01;
     R det = sxx * syy - sxy * sxy;
     if (!(det > R(0))) return P;
-    R a = syy / det;
-    R b = (-sxy) / det;
-    R c = sxx / det;
+    R idet = R(1) / det;
+    R a = syy * idet;
+    R b = (-sxy) * idet;
+    R c = sxx * idet;
     if (!std::isfinite(u) || !std::isfinite(v) || !std::isfinite(a) || !std::isfinite(b) || !std::isfinite(c))
         return P;
 
@@ -291,8 +296,9 @@ template <typename R> Proj<R> preprocess_one(const SceneIn& s, int64_t i, const 
     // View-dependent colour from W and h (degree <= 3), clamped at 0 after +0.5.
     R d0 = mu[0] - cam.campos[0], d1 = mu[1] - cam.campos[1], d2 = mu[2] - cam.campos[2];
     R len = std::sqrt((d0 * d0 + d1 * d1) + d2 * d2);
+    R ilen = R(1) / len;
     R Y[16];
-    sh_basis<R>(d0 / len, d1 / len, d2 / len, Y);
+    sh_basis<R>(d0 * ilen, d1 * ilen, d2 * ilen, Y);
     int nc = (s.sh_degree + 1) * (s.sh_degree + 1);
     for (int ch = 0; ch < 3; ++ch) {
         R acc = Y[0] * R(s.sh[(0 * 3 + ch) * n + i]);

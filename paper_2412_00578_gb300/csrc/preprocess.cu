@@ -115,13 +115,17 @@ __device__ __forceinline__ void preprocess_one(const PreArgs& A, const CamK& C, 
         const float n2 = ((qw * qw + qx * qx) + qy * qy) + qz * qz;
         ok = ok && (n2 > 0.0f);
         if (ok) {
-            const float xz = px / pz;
-            const float yz = py / pz;
+            // quotients by one denominator are products with its reciprocal
+            // (1/z, 1/|q|, 1/det, 1/|mu - campos|), as the oracle computes them
+            const float iz = 1.0f / pz;
+            const float xz = px * iz;
+            const float yz = py * iz;
             const float u = C.fx * xz + C.cx;
             const float v = C.fy * yz + C.cy;
             // rotation from the normalised quaternion
             const float nq = sqrtf(n2);
-            const float w = qw / nq, x = qx / nq, y = qy / nq, z = qz / nq;
+            const float inq = 1.0f / nq;
+            const float w = qw * inq, x = qx * inq, y = qy * inq, z = qz * inq;
             float R[9];
             R[0] = 1.0f - 2.0f * (y * y + z * z);
             R[1] = 2.0f * (x * y - w * z);
@@ -148,11 +152,11 @@ __device__ __forceinline__ void preprocess_one(const PreArgs& A, const CamK& C, 
             // Jacobian at the clamped mean
             const float tx = fminf(C.limx, fmaxf(-C.limx, xz)) * pz;
             const float ty = fminf(C.limy, fmaxf(-C.limy, yz)) * pz;
-            const float zz = pz * pz;
-            const float j00 = C.fx / pz;
-            const float j02 = -((C.fx * tx) / zz);
-            const float j11 = C.fy / pz;
-            const float j12 = -((C.fy * ty) / zz);
+            const float iz2 = iz * iz;
+            const float j00 = C.fx * iz;
+            const float j02 = -((C.fx * tx) * iz2);
+            const float j11 = C.fy * iz;
+            const float j12 = -((C.fy * ty) * iz2);
             float T0[3], T1[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -173,9 +177,10 @@ __device__ __forceinline__ void preprocess_one(const PreArgs& A, const CamK& C, 
             const float sxy = c01;
             const float det = sxx * syy - sxy * sxy;
             if (det > 0.0f) {
-                const float a = syy / det;
-                const float b = (-sxy) / det;
-                const float c = sxx / det;
+                const float idet = 1.0f / det;
+                const float a = syy * idet;
+                const float b = (-sxy) * idet;
+                const float c = sxx * idet;
                 if (isfinite(u) && isfinite(v) && isfinite(a) && isfinite(b) && isfinite(c)) {
                     const float t = 2.0f * gs_logf(255.0f * sigma);
                     const float mid = 0.5f * (sxx + syy);
@@ -189,8 +194,9 @@ __device__ __forceinline__ void preprocess_one(const PreArgs& A, const CamK& C, 
                         // SH colour, read only for Gaussians that touch a tile
                         const float d0 = mx - C.campos[0], d1 = my - C.campos[1], d2 = mz - C.campos[2];
                         const float len = sqrtf((d0 * d0 + d1 * d1) + d2 * d2);
+                        const float ilen = 1.0f / len;
                         float Y[16];
-                        sh_basis16(d0 / len, d1 / len, d2 / len, Y);
+                        sh_basis16(d0 * ilen, d1 * ilen, d2 * ilen, Y);
                         float rgb[3];
 #pragma unroll
                         for (int ch = 0; ch < 3; ++ch) {
