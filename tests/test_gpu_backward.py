@@ -107,9 +107,12 @@ def test_finite_differences_of_gpu_forward(raster):
             getattr(minus, key)[idx] = x0 - step
             he = (float(getattr(plus, key)[idx]) - float(getattr(minus, key)[idx])) / 2
             fds.append((L(plus) - L(minus)) / (2 * he))
-        if abs(fds[0] - fds[1]) > 2e-2 * max(abs(fds[1]), rms[key]):
-            continue  # crossed a threshold, clamp or stop decision
         denom = max(abs(fds[1]), 1e-2 * rms[key])
+        if abs(fds[0] - fds[1]) > 2e-2 * denom:
+            # the reference has not converged to the checked tolerance (a
+            # threshold, clamp or stop decision crossed, or FP32 noise in the
+            # difference quotient)
+            continue
         assert abs(g[key][idx] - fds[1]) / denom <= 2e-2, (key, idx, g[key][idx], fds)
         checked += 1
     assert checked >= 64
