@@ -41,7 +41,7 @@ ScratchLayout scratch_layout(int64_t ncap, int64_t kcap) {
     L.partials = off;
     off += align_up((scan_blocks_for(ncap) + 1) * 8);
     L.hist = off;
-    off += align_up((kMaxPasses * 256 + kMaxPasses) * 4);
+    off += align_up(kSortCtlWords * 4);
     L.lookback = off;
     off += align_up(2 * std::max<int64_t>(sort_partitions_for(kcap), 1) * 256 * 4);
     L.total = off;

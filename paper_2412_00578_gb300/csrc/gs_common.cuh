@@ -78,6 +78,10 @@ constexpr int kSortThreads = 512;
 constexpr int kSortItems = 8;
 constexpr int kSortPartition = kSortThreads * kSortItems;  // keys per onesweep partition
 constexpr int kMaxPasses = 12;
+// Sort control words at the start of the sort's scratch: [kMaxPasses][256]
+// digit totals, a partition ticket per pass, a ranking-method word per pass,
+// and the histogram kernel's block-completion counter.
+constexpr int kSortCtlWords = kMaxPasses * 256 + 2 * kMaxPasses + 1;
 
 // ---------------------------------------------------------------- elementary functions
 // Natural logarithm: frexp range reduction to m in [sqrt(1/2), sqrt(2)),

@@ -3,12 +3,15 @@
 //
 //   sort_hist   one read of the keys builds the digit histograms of every
 //               pass at once (shared-memory counters, one global atomic per
-//               bin per block) and clears the first look-back table.
+//               bin per block) and clears the first look-back table; the
+//               last block to finish picks each pass's ranking method from
+//               the finished histogram (below).
 //   sort_pass   one launch per digit.  Each block takes a 4096-key partition
 //               by atomic ticket (so partitions are processed in launch
 //               order and every predecessor is already resident), ranks its
-//               keys by digit stably (warp match + per-warp counters),
-//               publishes its per-digit counts, and resolves its global
+//               keys by digit stably (the lanes of a warp holding equal
+//               digits find each other, then per-warp counters), publishes
+//               its per-digit counts, and resolves its global
 //               offsets by decoupled look-back over its predecessors'
 //               published counts.  Keys are staged in shared memory in digit
 //               order so each digit's run is written to HBM contiguously.
@@ -18,6 +21,14 @@
 //
 // Bits sorted: the 32 depth bits plus ceil(log2(tiles)) tile bits, split
 // into an even number of passes so the result lands back in buffer 0.
+//
+// Finding the lanes with equal digits: warp match costs more the more
+// distinct digits a warp holds; a shared-memory atomicOr of each lane's bit
+// into its digit's word costs more the more lanes share a digit.  Both give
+// the same peer masks, so the ranks (and the sort) do not depend on the
+// choice.  A pass whose digits are spread out (collision probability
+// sum_d (n_d / K)^2 at most 1/32) ranks by atomicOr, a concentrated one (the
+// top depth byte, the top tile bits) by match.
 #include <algorithm>
 
 #include "gs_common.cuh"
@@ -43,8 +54,12 @@ struct HistArgs {
     const uint32_t* status;
     uint32_t* hist;        // [passes][256]
     uint32_t* lookback0;   // first pass's table, cleared here
+    uint32_t* method;      // [passes]: 1 = rank by warp match, 0 = by atomicOr
+    uint32_t* done;        // blocks finished (zero at launch)
     int passes, dbits;
 };
+
+constexpr uint32_t kRankMatch = 1u;
 
 __global__ void __launch_bounds__(256) sort_hist_kernel(const HistArgs A) {
     __shared__ uint32_t sh[kMaxPasses * 256];
@@ -74,6 +89,27 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const HistArgs A) {
     __syncthreads();
     for (int i = threadIdx.x; i < A.passes * 256; i += blockDim.x)
         if (sh[i]) atomicAdd(&A.hist[i], sh[i]);
+    // The last block to finish sees every block's counts and sets the
+    // passes' ranking methods (warp w handles passes w, w + 8, ...).
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(A.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31;
+    const double kk = (double)K * (double)K;
+    for (int p = threadIdx.x >> 5; p < A.passes; p += blockDim.x >> 5) {
+        double sq = 0.0;
+        for (int d = lane; d < 256; d += 32) {
+            const double c = (double)__ldcg(A.hist + p * 256 + d);
+            sq += c * c;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) A.method[p] = (sq * 32.0 > kk) ? kRankMatch : 0u;
+    }
 }
 
 struct PassArgs {
@@ -86,6 +122,7 @@ struct PassArgs {
     uint32_t* lookback;     // this pass's table [partitions][256]
     uint32_t* lookback_next;// next pass's table: this block clears its own row
     uint32_t* ticket;
+    const uint32_t* method; // this pass's ranking method (set by sort_hist)
     int shift, dbits;
 };
 
@@ -99,8 +136,16 @@ __device__ __forceinline__ uint32_t low_bytes_sum(unsigned long long x, int r) {
 }
 
 struct PassSmem {
-    uint64_t keys[kSortPartition];
-    uint32_t vals[kSortPartition];
+    union {
+        // keys and values in digit order, staged for the write-out
+        struct {
+            uint64_t keys[kSortPartition];
+            uint32_t vals[kSortPartition];
+        } st;
+        // ranking by atomicOr (before staging): per warp, three rotating
+        // arrays of 256 peer words, so one __syncwarp per round suffices
+        uint32_t peer[kSortThreads / 32][3][256];
+    };
     // per (warp, digit, round): how many of that round's 32 keys in that warp
     // have that digit (at most 32)
     uint8_t cnt[kSortThreads / 32][256][kSortItems];
@@ -144,11 +189,21 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
     PassSmem& S = *reinterpret_cast<PassSmem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) S.part = atomicAdd(A.ticket, 1u);
+    const bool by_match = __ldg(A.method) == kRankMatch;  // uniform over the launch
+    const uint32_t t = tid;
+    const bool digit_thread = t < 256;
+    const uint32_t hist_t = digit_thread ? __ldg(A.hist + t) : 0u;  // loaded early, used after ranking
     {
         uint4* c4 = reinterpret_cast<uint4*>(&S.cnt[0][0][0]);
         constexpr int n4 = (int)(sizeof(S.cnt) / sizeof(uint4));
 #pragma unroll
         for (int i = tid; i < n4; i += kSortThreads) c4[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (!by_match) {
+            uint4* p4 = reinterpret_cast<uint4*>(&S.peer[0][0][0]);
+            constexpr int np4 = (int)(sizeof(S.peer) / sizeof(uint4));
+#pragma unroll
+            for (int i = tid; i < np4; i += kSortThreads) p4[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
     }
     __syncthreads();
     const uint32_t K = frame_keys(A.status);
@@ -171,16 +226,30 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
         val[r] = ok ? A.vin[idx] : 0u;
     }
     // Rank, rounds independent of each other: lanes with equal digits in a
-    // round find each other (match), their rank among themselves is the
-    // number of lower lanes, and the lowest one records the group's size for
-    // (warp, digit, round).
+    // round find each other (warp match, or each lane ORs its bit into its
+    // digit's word and reads the word back), their rank among themselves is
+    // the number of lower lanes, and the lowest one records the group's size
+    // for (warp, digit, round).  With atomicOr, round r uses array r mod 3
+    // and clears its words of round r-1 after the round's __syncwarp (every
+    // lane has read them before it), so an array is clean again, behind
+    // another __syncwarp, when round r+2 uses it.
     const uint32_t lt_mask = (1u << lane) - 1u;
     uint32_t dig[kSortItems], lt[kSortItems];
+    uint32_t dprev = kNoDigit;
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const uint32_t idx = base + warp * (kSortItems * 32) + r * 32 + lane;
         const uint32_t d = idx < K ? (uint32_t)((key[r] >> A.shift) & mask) : kNoDigit;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t peers;
+        if (by_match) {
+            peers = __match_any_sync(0xffffffffu, d);
+        } else {
+            if (d != kNoDigit) atomicOr(&S.peer[warp][r % 3][d], 1u << lane);
+            __syncwarp();
+            peers = d != kNoDigit ? S.peer[warp][r % 3][d] : 0u;
+            if (dprev != kNoDigit) S.peer[warp][(r + 2) % 3][dprev] = 0u;
+            dprev = d;
+        }
         dig[r] = d;
         lt[r] = __popc(peers & lt_mask);
         if (d != kNoDigit && lt[r] == 0) S.cnt[warp][d][r] = (uint8_t)__popc(peers);
@@ -190,8 +259,6 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
     // the warps, block total, published aggregate (within a warp the rounds'
     // counts are summed again when keys are placed).  The other threads feed
     // zeros to the block scan.
-    const uint32_t t = tid;
-    const bool digit_thread = t < 256;
     uint32_t tot = 0;
     if (digit_thread) {
 #pragma unroll
@@ -208,7 +275,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
     // one scan for both the block's digit offsets (low 16 bits, at most 4096)
     // and the digits' global starts (high bits)
     const unsigned long long packed =
-        ((unsigned long long)(digit_thread ? A.hist[t] : 0u) << 16) | (unsigned long long)tot;
+        ((unsigned long long)hist_t << 16) | (unsigned long long)tot;
     const unsigned long long sc = block_excl_scan_u64(packed, S.warp_tmp);
     const uint32_t boff = (uint32_t)(sc & 0xffffull);
     const uint32_t dstart = (uint32_t)(sc >> 16);
@@ -222,8 +289,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
         if (d != kNoDigit) {
             const unsigned long long c = *reinterpret_cast<const unsigned long long*>(&S.cnt[warp][d][0]);
             const uint32_t pos = S.boff[d] + S.wpre[warp][d] + low_bytes_sum(c, r) + lt[r];
-            S.keys[pos] = key[r];
-            S.vals[pos] = val[r];
+            S.st.keys[pos] = key[r];
+            S.st.vals[pos] = val[r];
         }
     }
     if (digit_thread) {
@@ -269,12 +336,12 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
     __syncthreads();
     const uint32_t nvalid = min((uint32_t)kSortPartition, K - base);
     for (uint32_t i = tid; i < nvalid; i += kSortThreads) {
-        const uint64_t k = S.keys[i];
+        const uint64_t k = S.st.keys[i];
         const uint32_t d = (uint32_t)((k >> A.shift) & mask);
         const uint32_t o = S.gbase[d] + i;
         if (o < K) {  // always true unless a look-back wait timed out (flagged above)
             A.kout[o] = k;
-            A.vout[o] = S.vals[i];
+            A.vout[o] = S.st.vals[i];
         }
     }
 }
@@ -313,13 +380,13 @@ gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override) {
         attr_done[ctx->device & 63] = true;
     }
     // histograms and tickets start at zero
-    if (cudaMemsetAsync(v.sort_hist, 0, (kMaxPasses * 256 + kMaxPasses) * sizeof(uint32_t), ctx->stream) !=
-        cudaSuccess)
+    if (cudaMemsetAsync(v.sort_hist, 0, kSortCtlWords * sizeof(uint32_t), ctx->stream) != cudaSuccess)
         return set_error(ctx, GS_ERR_CUDA, "sort: cudaMemsetAsync failed");
     if (v.kcap == 0) return GS_OK;
     const int64_t parts = sort_partitions_for(v.kcap);
     const size_t table = (size_t)v.sort_partitions * 256;
-    HistArgs H{v.keys0, v.status, v.sort_hist, v.sort_lookback, passes, dbits};
+    uint32_t* method = v.sort_hist + kMaxPasses * 256 + kMaxPasses;
+    HistArgs H{v.keys0, v.status, v.sort_hist, v.sort_lookback, method, method + kMaxPasses, passes, dbits};
     int hblocks = (int)std::min<int64_t>((v.kcap + 2047) / 2048, (int64_t)ctx->num_sms * 8);
     if (hblocks < 1) hblocks = 1;
     sort_hist_kernel<<<hblocks, 256, 0, ctx->stream>>>(H);
@@ -336,6 +403,7 @@ gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override) {
         A.lookback = v.sort_lookback + (even ? 0 : table);
         A.lookback_next = (p + 1 < passes) ? v.sort_lookback + (even ? table : 0) : nullptr;
         A.ticket = v.sort_hist + kMaxPasses * 256 + p;
+        A.method = method + p;
         A.shift = p * dbits;
         A.dbits = dbits;
         sort_pass_kernel<<<(unsigned)parts, kSortThreads, sizeof(PassSmem), ctx->stream>>>(A);
