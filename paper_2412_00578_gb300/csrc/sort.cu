@@ -126,15 +126,6 @@ struct PassArgs {
     int shift, dbits;
 };
 
-static_assert(kSortItems == 8, "a warp's 8 per-round digit counts are read as one 64-bit word");
-
-// Sum of the low r bytes of x (r <= 7, each byte <= 32, so the sum fits a byte).
-__device__ __forceinline__ uint32_t low_bytes_sum(unsigned long long x, int r) {
-    if (r == 0) return 0u;
-    const unsigned long long m = (r >= 8) ? ~0ull : ((1ull << (8 * r)) - 1ull);
-    return (uint32_t)(((x & m) * 0x0101010101010101ull) >> 56);
-}
-
 struct PassSmem {
     union {
         // keys and values in digit order, staged for the write-out
@@ -146,12 +137,10 @@ struct PassSmem {
         // arrays of 256 peer words, so one __syncwarp per round suffices
         uint32_t peer[kSortThreads / 32][3][256];
     };
-    // per (warp, digit, round): how many of that round's 32 keys in that warp
-    // have that digit (at most 32)
-    uint8_t cnt[kSortThreads / 32][256][kSortItems];
-    // per (warp, digit): keys with that digit in earlier warps of the partition
-    uint16_t wpre[kSortThreads / 32][256];
-    uint32_t boff[256];
+    // per (warp, digit): while ranking, the warp's keys with that digit so
+    // far; after the digit scan, the staging slot of the warp's first key
+    // with that digit (the digit's block offset plus the earlier warps' keys)
+    uint32_t wbase[kSortThreads / 32][256];
     uint32_t gbase[256];
     unsigned long long warp_tmp[32];
     uint32_t part;
@@ -194,8 +183,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
     const bool digit_thread = t < 256;
     const uint32_t hist_t = digit_thread ? __ldg(A.hist + t) : 0u;  // loaded early, used after ranking
     {
-        uint4* c4 = reinterpret_cast<uint4*>(&S.cnt[0][0][0]);
-        constexpr int n4 = (int)(sizeof(S.cnt) / sizeof(uint4));
+        uint4* c4 = reinterpret_cast<uint4*>(&S.wbase[0][0]);
+        constexpr int n4 = (int)(sizeof(S.wbase) / sizeof(uint4));
 #pragma unroll
         for (int i = tid; i < n4; i += kSortThreads) c4[i] = make_uint4(0u, 0u, 0u, 0u);
         if (!by_match) {
@@ -225,16 +214,18 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
         key[r] = ok ? A.kin[idx] : 0ull;
         val[r] = ok ? A.vin[idx] : 0u;
     }
-    // Rank, rounds independent of each other: lanes with equal digits in a
-    // round find each other (warp match, or each lane ORs its bit into its
-    // digit's word and reads the word back), their rank among themselves is
-    // the number of lower lanes, and the lowest one records the group's size
-    // for (warp, digit, round).  With atomicOr, round r uses array r mod 3
-    // and clears its words of round r-1 after the round's __syncwarp (every
-    // lane has read them before it), so an array is clean again, behind
-    // another __syncwarp, when round r+2 uses it.
+    // Rank within the warp, round by round: lanes with equal digits in a round
+    // find each other (warp match, or each lane ORs its bit into its digit's
+    // word and reads the word back); the lowest of them adds the group's size
+    // to the warp's counter for that digit, and the counter's old value plus
+    // the number of lower lanes in the group is each key's rank among the
+    // warp's keys with that digit.  A __syncwarp separates one round's
+    // counter updates from the next round's.  With atomicOr, round r uses
+    // array r mod 3 and clears its words of round r-1 after the round's
+    // __syncwarp (every lane has read them before it), so an array is clean
+    // again, behind another __syncwarp, when round r+2 uses it.
     const uint32_t lt_mask = (1u << lane) - 1u;
-    uint32_t dig[kSortItems], lt[kSortItems];
+    uint32_t rank[kSortItems];  // kNoDigit past the last key
     uint32_t dprev = kNoDigit;
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
@@ -242,6 +233,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
         const uint32_t d = idx < K ? (uint32_t)((key[r] >> A.shift) & mask) : kNoDigit;
         uint32_t peers;
         if (by_match) {
+            __syncwarp();
             peers = __match_any_sync(0xffffffffu, d);
         } else {
             if (d != kNoDigit) atomicOr(&S.peer[warp][r % 3][d], 1u << lane);
@@ -250,23 +242,20 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
             if (dprev != kNoDigit) S.peer[warp][(r + 2) % 3][dprev] = 0u;
             dprev = d;
         }
-        dig[r] = d;
-        lt[r] = __popc(peers & lt_mask);
-        if (d != kNoDigit && lt[r] == 0) S.cnt[warp][d][r] = (uint8_t)__popc(peers);
+        const uint32_t lt = __popc(peers & lt_mask);
+        uint32_t before = 0u;
+        if (d != kNoDigit && lt == 0) before = atomicAdd(&S.wbase[warp][d], (uint32_t)__popc(peers));
+        const int leader = peers ? __ffs(peers) - 1 : lane;
+        before = __shfl_sync(0xffffffffu, before, leader);
+        rank[r] = d != kNoDigit ? before + lt : kNoDigit;
     }
     __syncthreads();
-    // Per digit (threads 0..255, thread t <-> digit t): exclusive prefix over
-    // the warps, block total, published aggregate (within a warp the rounds'
-    // counts are summed again when keys are placed).  The other threads feed
-    // zeros to the block scan.
+    // Per digit (threads 0..255, thread t <-> digit t): block total and
+    // published aggregate.  The other threads feed zeros to the block scan.
     uint32_t tot = 0;
     if (digit_thread) {
 #pragma unroll
-        for (int w = 0; w < kSortThreads / 32; ++w) {
-            const unsigned long long c = *reinterpret_cast<const unsigned long long*>(&S.cnt[w][t][0]);
-            S.wpre[w][t] = (uint16_t)tot;
-            tot += low_bytes_sum(c, 7) + (uint32_t)(c >> 56);
-        }
+        for (int w = 0; w < kSortThreads / 32; ++w) tot += S.wbase[w][t];
         st_relaxed_gpu(A.lookback + (size_t)part * 256 + t, (part == 0 ? kFlagPrefix : kFlagAgg) | tot);
         // clear this partition's row of the next pass's table (that table's last
         // user was the previous pass, which has completed)
@@ -279,18 +268,39 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
     const unsigned long long sc = block_excl_scan_u64(packed, S.warp_tmp);
     const uint32_t boff = (uint32_t)(sc & 0xffffull);
     const uint32_t dstart = (uint32_t)(sc >> 16);
-    if (digit_thread) S.boff[t] = boff;
+    // Per digit: the staging slot of each warp's first key with the digit.
+    // The counters are read in batches of 8 warps ahead of the stores: the
+    // compiler cannot tell that the stores miss the words still to be read,
+    // so a read after a store would wait for it.
+    if (digit_thread) {
+        constexpr int kBatch = 8;
+        static_assert((kSortThreads / 32) % kBatch == 0, "warps come in batches of 8");
+        uint32_t run = boff;
+#pragma unroll
+        for (int w0 = 0; w0 < kSortThreads / 32; w0 += kBatch) {
+            uint32_t c[kBatch];
+#pragma unroll
+            for (int w = 0; w < kBatch; ++w) c[w] = S.wbase[w0 + w][t];
+#pragma unroll
+            for (int w = 0; w < kBatch; ++w) {
+                S.wbase[w0 + w][t] = run;
+                run += c[w];
+            }
+        }
+    }
     __syncthreads();
     // Stage in digit order (positions are block-local, so this does not wait
-    // for the look-back, and it frees the key registers before it).
+    // for the look-back, and it frees the key registers before it).  All
+    // positions are computed before the first store, so the reads overlap.
+    uint32_t pos[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r)
+        pos[r] = rank[r] != kNoDigit ? S.wbase[warp][(uint32_t)(key[r] >> A.shift) & mask] + rank[r] : kNoDigit;
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
-        const uint32_t d = dig[r];
-        if (d != kNoDigit) {
-            const unsigned long long c = *reinterpret_cast<const unsigned long long*>(&S.cnt[warp][d][0]);
-            const uint32_t pos = S.boff[d] + S.wpre[warp][d] + low_bytes_sum(c, r) + lt[r];
-            S.st.keys[pos] = key[r];
-            S.st.vals[pos] = val[r];
+        if (pos[r] != kNoDigit) {
+            S.st.keys[pos[r]] = key[r];
+            S.st.vals[pos[r]] = val[r];
         }
     }
     if (digit_thread) {
@@ -335,7 +345,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
     }
     __syncthreads();
     const uint32_t nvalid = min((uint32_t)kSortPartition, K - base);
-    for (uint32_t i = tid; i < nvalid; i += kSortThreads) {
+    auto put = [&](uint32_t i) {
         const uint64_t k = S.st.keys[i];
         const uint32_t d = (uint32_t)((k >> A.shift) & mask);
         const uint32_t o = S.gbase[d] + i;
@@ -343,6 +353,12 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
             A.kout[o] = k;
             A.vout[o] = S.st.vals[i];
         }
+    };
+    if (nvalid == (uint32_t)kSortPartition) {
+#pragma unroll
+        for (int u = 0; u < kSortItems; ++u) put(tid + (uint32_t)u * kSortThreads);
+    } else {
+        for (uint32_t i = tid; i < nvalid; i += kSortThreads) put(i);
     }
 }
 
