@@ -196,6 +196,24 @@ def test_one_crowded_tile(raster, rast, n):
     assert r[1 * 4 + 1, 1] - r[1 * 4 + 1, 0] == K  # all of them in tile (1, 1)
 
 
+def test_one_depth_for_the_whole_frame(raster, rast):
+    """30,000 Gaussians on the plane z = 0 seen from z = 5: every key has the
+    same depth bits, so each depth digit pass holds a single digit value (the
+    sort's concentrated-digit ranking at its extreme) and every tile's order is
+    Gaussian index order, decided by the sort's stability alone."""
+    scene = synth.uniform_box_scene(30000, seed=61, half=2.0, log_scale_mu=-3.5, log_scale_sd=0.6)
+    scene.means[2] = 0.0
+    cam = synth.pinhole(320, 240, 60.0, np.eye(3), np.array([0.0, 0.0, 5.0]))
+    gpu = run_pipeline(raster, rast, scene, cam, 2, 16)
+    depth_bits = np.unique(gpu["keys_unsorted"] & np.uint64(0xFFFFFFFF))
+    assert depth_bits.size == 1 and gpu["K"] > 30000  # precondition: one depth, many keys
+    check_against_oracle(gpu, scene, cam, 2, 16)
+    # within each tile the values ascend
+    tiles = gpu["keys"] >> np.uint64(32)
+    same = tiles[1:] == tiles[:-1]
+    assert np.all(gpu["vals"][1:][same] > gpu["vals"][:-1][same])
+
+
 @pytest.mark.parametrize("digits", [6, 5, 4])
 def test_digit_widths_agree(raster, rast, digits):
     """Narrower radix digits (more passes) give the same sorted pairs, bit for
