@@ -316,7 +316,7 @@ def outdoor():
     return synth.outdoor_workload()
 
 
-@pytest.mark.parametrize("mode", [2, 0])
+@pytest.mark.parametrize("mode", [2, 1, 0])
 def test_outdoor_3m_1280x840_full_frame(raster, outdoor, mode):
     """The 3M-Gaussian 1280x840 workload in the launch configuration the
     benchmark times (gs_forward, tile 16): every key, range and pixel."""
