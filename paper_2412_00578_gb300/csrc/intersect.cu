@@ -44,6 +44,7 @@ __device__ __forceinline__ long long block_excl_scan(long long v, long long* s_w
 
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const int32_t* __restrict__ counts, int64_t n,
                                                                    long long* __restrict__ partials) {
+    pdl_begin();
     __shared__ long long s_warp[32];
     const int64_t base = (int64_t)blockIdx.x * kScanBlock;
     long long sum = 0;
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const int32_t
 
 __global__ void __launch_bounds__(1024) scan_top_kernel(long long* __restrict__ partials, int64_t nblocks,
                                                         int64_t kcap, uint32_t* __restrict__ status, bool clear3) {
+    pdl_begin();
     __shared__ long long s_warp[32];
     __shared__ long long s_carry;
     if (threadIdx.x == 0) s_carry = 0;
@@ -139,6 +141,7 @@ struct KeyWriter {
 
 template <bool kMulti>
 __global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
+    pdl_begin();
     __shared__ long long s_warp[32];
     if (A.status[2] & GS_FLAG_CAPACITY) return;  // keys do not fit: emit nothing
     if (kMulti && A.status[3]) return;           // cameras do not fit the batch frame
@@ -223,10 +226,12 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
 gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v) {
     const int64_t nb = scan_blocks_for(v.ncap);
     if (nb > 0) {
-        scan_reduce_kernel<<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(v.counts, v.ncap, v.scan_partials);
+        (void)launch_pdl(ctx->stream, scan_reduce_kernel, dim3((unsigned)nb), dim3(kScanThreads), 0, v.counts, v.ncap,
+                         v.scan_partials);
         ctx->launches += 1;
     }
-    scan_top_kernel<<<1, 1024, 0, ctx->stream>>>(v.scan_partials, nb, v.kcap, v.status, v.table == nullptr);
+    (void)launch_pdl(ctx->stream, scan_top_kernel, dim3(1), dim3(1024), 0, v.scan_partials, nb, v.kcap, v.status,
+                     v.table == nullptr);
     ctx->launches += 1;
     if (nb > 0) {
         EmitArgs A;
@@ -243,8 +248,8 @@ gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const Fram
         A.grid = Grid{(float)v.tile, v.gx, v.gy};
         A.table = v.table;
         A.cam_stride = v.cam_stride;
-        if (v.table) emit_kernel<true><<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(A);
-        else emit_kernel<false><<<(unsigned)nb, kScanThreads, 0, ctx->stream>>>(A);
+        if (v.table) (void)launch_pdl(ctx->stream, emit_kernel<true>, dim3((unsigned)nb), dim3(kScanThreads), 0, A);
+        else (void)launch_pdl(ctx->stream, emit_kernel<false>, dim3((unsigned)nb), dim3(kScanThreads), 0, A);
         ctx->launches += 1;
     }
     return check_launch(ctx, "intersect");

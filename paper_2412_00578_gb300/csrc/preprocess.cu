@@ -225,6 +225,7 @@ __device__ __forceinline__ void preprocess_one(const PreArgs& A, const CamK& C, 
 }
 
 __global__ void __launch_bounds__(256, 4) preprocess_kernel(const PreArgs A) {
+    pdl_begin();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.ncap) return;
     preprocess_one(A, A.cam, A.grid, i, i);
@@ -284,7 +285,7 @@ gs_status launch_preprocess(gs_context* ctx, const gs_scene* s, const gs_camera*
     }
     if (v.ncap == 0) return GS_OK;
     const int64_t blocks = (v.ncap + threads - 1) / threads;
-    preprocess_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(A);
+    (void)launch_pdl(ctx->stream, preprocess_kernel, dim3((unsigned)blocks), dim3(threads), 0, A);
     ctx->launches += 1;
     return check_launch(ctx, "preprocess");
 }

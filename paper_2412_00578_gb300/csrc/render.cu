@@ -35,6 +35,7 @@ __device__ __forceinline__ uint32_t frame_keys_r(const uint32_t* status) {
 // predecessor's closes the previous range and opens its own.
 __global__ void __launch_bounds__(256) ranges_kernel(const uint64_t* __restrict__ keys,
                                                      const uint32_t* __restrict__ status, uint2* __restrict__ ranges) {
+    pdl_begin();
     const uint32_t K = frame_keys_r(status);
     const uint32_t i0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4u;
     if (i0 >= K) return;
@@ -109,6 +110,7 @@ __device__ __forceinline__ int camera_of_tile(const CamRec* table, int num_cams,
 // rest of the GPU idle while they finish.
 __global__ void __launch_bounds__(1024) tile_order_kernel(const uint2* __restrict__ ranges, uint32_t tiles,
                                                          uint32_t* __restrict__ order) {
+    pdl_begin();
     __shared__ uint32_t cnt[33];
     __shared__ uint32_t base[33];
     __shared__ uint8_t s_cls[kMaxOrderedTiles];  // class of each tile, read once from ranges
@@ -160,6 +162,7 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const uint2* __restric
 
 template <int T, bool kStats, bool kMulti>
 __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 4 : 16)) blend_kernel(const BlendArgs A) {
+    pdl_begin();
     constexpr int NT = T * T;
     constexpr int NB = NT < 256 ? NT : 256;  // Gaussians per shared-memory batch
     constexpr int NSX = T / kSubW;
@@ -337,11 +340,12 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 4 : 16)) blend_
 
 gs_status launch_ranges(gs_context* ctx, const FrameView& v) {
     const size_t tiles = (size_t)v.gx * v.gy;
-    if (cudaMemsetAsync(v.ranges, 0, tiles * sizeof(uint2), ctx->stream) != cudaSuccess)
-        return set_error(ctx, GS_ERR_CUDA, "tile_ranges: cudaMemsetAsync failed");
+    (void)launch_pdl(ctx->stream, zero_words_kernel, dim3(zero_blocks(2 * (int64_t)tiles)), dim3(256), 0,
+                     reinterpret_cast<uint32_t*>(v.ranges), 2 * (int64_t)tiles);
+    ctx->launches += 1;
     if (v.kcap == 0) return GS_OK;
     const int64_t blocks = (v.kcap + 1023) / 1024;  // 4 keys per thread
-    ranges_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(v.keys0, v.status, v.ranges);
+    (void)launch_pdl(ctx->stream, ranges_kernel, dim3((unsigned)blocks), dim3(256), 0, v.keys0, v.status, v.ranges);
     ctx->launches += 1;
     return check_launch(ctx, "tile_ranges");
 }
@@ -351,7 +355,7 @@ const uint32_t* launch_tile_order(gs_context* ctx, const FrameView& v) {
     // sort, which clears every word of it that it reads before reading it.
     const unsigned tiles = (unsigned)(v.gx * v.gy);
     if (tiles == 0 || tiles > kMaxOrderedTiles || (int64_t)tiles > 2 * v.sort_partitions * 256) return nullptr;
-    tile_order_kernel<<<1, 1024, 0, ctx->stream>>>(v.ranges, tiles, v.sort_lookback);
+    (void)launch_pdl(ctx->stream, tile_order_kernel, dim3(1), dim3(1024), 0, v.ranges, tiles, v.sort_lookback);
     ctx->launches += 1;
     return v.sort_lookback;
 }
@@ -380,7 +384,8 @@ gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameVi
     const unsigned tiles = (unsigned)(v.gx * v.gy);
     if (tiles == 0) return GS_OK;
     A.order = launch_tile_order(ctx, v);
-#define GS_BLEND_LAUNCH(T_, S_, M_) blend_kernel<T_, S_, M_><<<tiles, T_ * T_, 0, ctx->stream>>>(A)
+#define GS_BLEND_LAUNCH(T_, S_, M_) \
+    (void)launch_pdl(ctx->stream, blend_kernel<T_, S_, M_>, dim3(tiles), dim3(T_ * T_), 0, A)
 #define GS_BLEND_TILES(S_, M_)                                                             \
     switch (v.tile) {                                                                      \
         case 8: GS_BLEND_LAUNCH(8, S_, M_); break;                                         \

@@ -62,6 +62,7 @@ struct HistArgs {
 constexpr uint32_t kRankMatch = 1u;
 
 __global__ void __launch_bounds__(256) sort_hist_kernel(const HistArgs A) {
+    pdl_begin();
     __shared__ uint32_t sh[kMaxPasses * 256];
     for (int i = threadIdx.x; i < A.passes * 256; i += blockDim.x) sh[i] = 0;
     __syncthreads();
@@ -174,6 +175,7 @@ __device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long 
 }
 
 __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassArgs A) {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PassSmem& S = *reinterpret_cast<PassSmem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -396,8 +398,9 @@ gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override) {
         attr_done[ctx->device & 63] = true;
     }
     // histograms and tickets start at zero
-    if (cudaMemsetAsync(v.sort_hist, 0, kSortCtlWords * sizeof(uint32_t), ctx->stream) != cudaSuccess)
-        return set_error(ctx, GS_ERR_CUDA, "sort: cudaMemsetAsync failed");
+    (void)launch_pdl(ctx->stream, zero_words_kernel, dim3(zero_blocks(kSortCtlWords)), dim3(256), 0, v.sort_hist,
+                     (int64_t)kSortCtlWords);
+    ctx->launches += 1;
     if (v.kcap == 0) return GS_OK;
     const int64_t parts = sort_partitions_for(v.kcap);
     const size_t table = (size_t)v.sort_partitions * 256;
@@ -405,7 +408,7 @@ gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override) {
     HistArgs H{v.keys0, v.status, v.sort_hist, v.sort_lookback, method, method + kMaxPasses, passes, dbits};
     int hblocks = (int)std::min<int64_t>((v.kcap + 2047) / 2048, (int64_t)ctx->num_sms * 8);
     if (hblocks < 1) hblocks = 1;
-    sort_hist_kernel<<<hblocks, 256, 0, ctx->stream>>>(H);
+    (void)launch_pdl(ctx->stream, sort_hist_kernel, dim3(hblocks), dim3(256), 0, H);
     ctx->launches += 1;
     for (int p = 0; p < passes; ++p) {
         PassArgs A;
@@ -422,7 +425,7 @@ gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override) {
         A.method = method + p;
         A.shift = p * dbits;
         A.dbits = dbits;
-        sort_pass_kernel<<<(unsigned)parts, kSortThreads, sizeof(PassSmem), ctx->stream>>>(A);
+        (void)launch_pdl(ctx->stream, sort_pass_kernel, dim3((unsigned)parts), dim3(kSortThreads), sizeof(PassSmem), A);
         ctx->launches += 1;
     }
     return check_launch(ctx, "sort");
