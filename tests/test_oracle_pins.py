@@ -457,3 +457,76 @@ def test_blend_pair_counts():
     assert acc["contributing_pairs"] == snug["contributing_pairs"]
     assert snug["evaluated_pairs"] >= acc["evaluated_pairs"]
     assert acc["evaluated_pairs"] > acc["contributing_pairs"] > 0
+
+
+# ---------------------------------------------------------------- 3-sigma rectangle
+def sigma3_golden():
+    path = __file__.replace("test_oracle_pins.py", "golden/sigma3_cases.txt")
+    cases = []
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        name, rest = line.split(":", 1)
+        nums, rect = rest.split("|")
+        u, v, r, T, gx, gy = (float(x) for x in nums.split())
+        x0, x1, y0, y1 = (int(x) for x in rect.split())
+        want = {(tx, ty) for ty in range(y0, y1) for tx in range(x0, x1)}
+        cases.append((name, (u, v, 1.0, 0.0, 1.0, 1.0, r), int(T), int(gx), int(gy), want))
+    return cases
+
+
+def sigma3_failures(tiles_fn):
+    bad = []
+    for name, e, T, gx, gy, want in sigma3_golden():
+        for prec64 in (True, False):
+            got = tile_set(tiles_fn(e, SIG3, T, gx, gy, prec64))
+            if got != want:
+                bad.append((name, prec64, sorted(got), sorted(want)))
+    return bad
+
+
+def test_sigma3_rectangle_golden():
+    """The 3-sigma square's tile rectangle (Sec. 4.1, Eq. radius, Fig. 2a:
+    the 3D-GS rule) on hand-derived cases where its bounds land on, half a
+    pixel before and one pixel past tile edges, near 0 and past the grid
+    (tests/golden/sigma3_cases.txt derives each expected rectangle)."""
+    assert len(sigma3_golden()) >= 20
+    assert sigma3_failures(oracle.ellipse_tiles) == []
+
+
+# Plausible slips in the rectangle: each planted into a copy of the oracle
+# source (never into oracle.cpp itself) must fail the golden cases above.
+SIGMA3_MUTANTS = {
+    "max_plus_T": ("(P.u + r + (T - R(1))) / T", "(P.u + r + T) / T"),
+    "max_floor_as_ceil": ("return static_cast<int>(x);  // truncation toward zero",
+                          "return static_cast<int>(std::ceil(x));"),
+    "min_plus_half": ("tr((P.u - r) / T, g.gx)", "tr((P.u - r + R(0.5)) / T, g.gx)"),
+    "y_max_plus_T": ("(P.v + r + (T - R(1))) / T", "(P.v + r + T) / T"),
+}
+
+
+@pytest.mark.parametrize("mutant", sorted(SIGMA3_MUTANTS))
+def test_sigma3_golden_catches_planted_mistakes(mutant, tmp_path):
+    import ctypes
+    import subprocess
+
+    src = oracle._SRC.read_text()
+    old, new = SIGMA3_MUTANTS[mutant]
+    assert src.count(old) == 1, f"pattern for {mutant} not found exactly once"
+    mut = tmp_path / "oracle_mutant.cpp"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "liboracle_mutant.so"
+    subprocess.run(["g++", *oracle.CXXFLAGS, str(mut), "-o", str(so)], check=True)
+    L = ctypes.CDLL(str(so))
+    oracle._declare(L)
+
+    def tiles(e, mode, T, gx, gy, prec64):
+        ee = np.zeros(7, np.float64)
+        ee[:len(e)] = e
+        cap = gx * gy + 1
+        out = np.zeros((cap, 2), np.int32)
+        k = L.oracle_ellipse_tiles(int(prec64), mode, 0, oracle._ptr(ee), T, gx, gy, oracle._ptr(out), cap)
+        return out[:k].copy()
+
+    assert sigma3_failures(tiles), f"planted mistake {mutant} passed every golden case"
