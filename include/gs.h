@@ -248,7 +248,9 @@ gs_status gs_render_backward(gs_context* ctx, const gs_scene* scene, const gs_ca
  * gs_intersect.  It does the same work and writes the same keys[0]/vals[0],
  * but keeps its working memory (running sums of the counts and status words)
  * in a fixed array built into the library instead of frame->scratch, which
- * may be NULL and is never touched.
+ * may be NULL and is never touched.  Of the frame's buffers only proj,
+ * counts, keys and vals are used and must be non-NULL; ranges, image,
+ * final_T and last may be NULL.
  *   - Limit: frame->n_capacity <= 16,777,216 (GS_ERR_INVALID beyond, with a
  *     message); the array takes about 131 KB on every device that loads the
  *     library, until the process exits.

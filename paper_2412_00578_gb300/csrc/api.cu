@@ -72,7 +72,7 @@ gs_status check_cfg(gs_context* ctx, const gs_raster_cfg* cfg, const gs_frame* f
 
 }  // namespace
 
-bool make_view(gs_context* ctx, const gs_frame* f, FrameView* v) {
+bool make_view(gs_context* ctx, const gs_frame* f, FrameView* v, unsigned need) {
     if (!f) {
         set_error(ctx, GS_ERR_INVALID, "frame is NULL");
         return false;
@@ -83,8 +83,9 @@ bool make_view(gs_context* ctx, const gs_frame* f, FrameView* v) {
                   f->height, (long long)f->n_capacity, (long long)f->key_capacity);
         return false;
     }
-    if (!f->proj || !f->counts || !f->keys || !f->vals || !f->ranges || !f->image || !f->final_T || !f->last ||
-        !f->scratch) {
+    const bool render_bufs = need == kNeedAll;
+    if (!f->proj || !f->counts || !f->keys || !f->vals || !f->scratch ||
+        (render_bufs && (!f->ranges || !f->image || !f->final_T || !f->last))) {
         set_error(ctx, GS_ERR_INVALID, "frame has a NULL buffer");
         return false;
     }
@@ -257,9 +258,9 @@ gs_status gs_render_stats(gs_context* ctx, const gs_camera* cam, const gs_raster
         return set_error(ctx, GS_ERR_CUDA, "render_stats: cudaMemsetAsync failed");
     if ((st = launch_render(ctx, cfg, v, counters))) return st;
     unsigned long long h[3] = {0, 0, 0};
-    if (cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
-        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
-        return set_error(ctx, GS_ERR_CUDA, "render_stats: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaError_t e = cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return set_error(ctx, GS_ERR_CUDA, "render_stats: %s", cudaGetErrorString(e));
     if (evaluated) *evaluated = h[0];
     if (contributed) *contributed = h[1];
     if (executed) *executed = h[2];
@@ -305,9 +306,9 @@ gs_status gs_read_status(gs_context* ctx, const gs_frame* frame, int64_t* num_ke
     FrameView v;
     if (!make_view(ctx, frame, &v)) return GS_ERR_INVALID;
     uint32_t w[3] = {0, 0, 0};
-    if (cudaMemcpyAsync(w, v.status, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
-        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
-        return set_error(ctx, GS_ERR_CUDA, "read_status: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaError_t e = cudaMemcpyAsync(w, v.status, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return set_error(ctx, GS_ERR_CUDA, "read_status: %s", cudaGetErrorString(e));
     const int64_t K = (int64_t)w[0] | ((int64_t)w[1] << 32);
     if (num_keys) *num_keys = K;
     if (flags) *flags = w[2];

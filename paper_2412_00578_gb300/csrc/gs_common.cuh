@@ -228,7 +228,10 @@ namespace gs {
 // host helpers (api.cu)
 gs_status set_error(gs_context* ctx, gs_status st, const char* fmt, ...);
 gs_status check_launch(gs_context* ctx, const char* what);
-bool make_view(gs_context* ctx, const gs_frame* f, FrameView* v);
+// Buffers a stage needs (make_view rejects a NULL one among them).
+constexpr unsigned kNeedAll = 0xffu;
+constexpr unsigned kNeedEmit = 1u;  // proj, counts, keys, vals only
+bool make_view(gs_context* ctx, const gs_frame* f, FrameView* v, unsigned need = kNeedAll);
 int sort_tile_bits(int64_t tiles);
 void sort_plan(int64_t tiles, int digit_override, int* passes, int* digit_bits);
 

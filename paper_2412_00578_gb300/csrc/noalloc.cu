@@ -84,7 +84,7 @@ extern "C" gs_status gs_intersect_noalloc(gs_context* ctx, const gs_camera* cam,
     gs_frame f = *frame;
     f.scratch = scratch;  // the caller's scratch pointer is neither needed nor touched
     FrameView v;
-    if (!make_view(ctx, &f, &v)) return GS_ERR_INVALID;
+    if (!make_view(ctx, &f, &v, kNeedEmit)) return GS_ERR_INVALID;
     // the intersect stage only touches the status words and the running sums
     const unsigned char* end = reinterpret_cast<const unsigned char*>(v.scan_partials) +
                                (scan_blocks_for(v.ncap) + 1) * (int64_t)sizeof(long long);
@@ -93,9 +93,9 @@ extern "C" gs_status gs_intersect_noalloc(gs_context* ctx, const gs_camera* cam,
         return set_error(ctx, GS_ERR_INVALID, "intersect_noalloc: working-memory layout does not fit");
     if ((st = launch_intersect(ctx, cfg, v))) return st;  // clears the status words first
     uint32_t w[3] = {0, 0, 0};
-    if (cudaMemcpyAsync(w, v.status, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
-        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
-        return set_error(ctx, GS_ERR_CUDA, "intersect_noalloc: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaError_t e = cudaMemcpyAsync(w, v.status, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return set_error(ctx, GS_ERR_CUDA, "intersect_noalloc: %s", cudaGetErrorString(e));
     *num_keys = (int64_t)w[0] | ((int64_t)w[1] << 32);
     if (w[2] & GS_FLAG_CAPACITY)
         return set_error(ctx, GS_ERR_CAPACITY, "%lld keys exceed key_capacity %lld", (long long)*num_keys,

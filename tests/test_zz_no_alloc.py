@@ -39,6 +39,8 @@ def test_intersect_noalloc_matches_intersect_on_two_calls_in_a_row():
         out.keys.fill_(-1)
         fs = raster.GsFrame.from_buffer_copy(out.struct)
         fs.scratch = None  # the caller provides no working memory at all
+        # nor the buffers of the later stages, which this stage never touches
+        fs.ranges = fs.image = fs.final_T = fs.last = None
         K = rast.gs_intersect_noalloc(cam, cfg, fs)
         torch.cuda.synchronize()
         assert K == K_ref > 0
