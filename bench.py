@@ -15,10 +15,11 @@ Multi-GPU (torchrun, N ranks): every rank renders its own frames of a full
 replica of the scene (the path does not shard a frame); value = frames of all
 ranks / max elapsed.
 
-``--impl reference`` times the CPU oracle (single thread, FP32, the
-documented operation order) on the host cores on the same workload; each step
-renders one horizontal band of the frame through the whole oracle pipeline,
-so the run stays within minutes; value = 1 / (bands x mean band time).
+``--impl reference`` times the CPU oracle (FP32, the documented operation
+order, built with OpenMP over its independent loops, all host cores) on the
+same workload; each step renders the frame, or one horizontal band of it when
+a frame is slow, through the whole oracle pipeline, so the run stays within
+minutes; value = 1 / (bands x mean band time).
 """
 from __future__ import annotations
 
@@ -59,7 +60,8 @@ def parse():
     p.add_argument("--mv-n", type=int, default=1_500_000)
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-backward", action="store_true")
-    p.add_argument("--serve-duration", type=float, default=1.5, help="seconds of arrivals per rate")
+    p.add_argument("--no-configs", action="store_true", help="skip the 16k-box and 300k-prune mode tables")
+    p.add_argument("--serve-duration", type=float, default=10.0, help="seconds of arrivals per rate")
     p.add_argument("--serve-rates", default="200,500,1000,2000")
     a = p.parse_args()
     a.steps = max(a.steps, 1)
@@ -241,19 +243,19 @@ def run_reference(args):
     import oracle
     from paper_2412_00578_gb300 import synth
 
-    oracle.build()
+    oracle.build(omp=True)
+    cores = os.cpu_count() or 1
     scene, cam = workload(args)
     H = cam.height
 
     def band_cam(y0, h):
-        c = synth.Camera(cam.width, h, cam.fx, cam.fy, cam.cx, cam.cy - y0, cam.tan_fovx, cam.tan_fovy,
-                         cam.viewmat, cam.campos, cam.near_z)
-        return c
+        return synth.Camera(cam.width, h, cam.fx, cam.fy, cam.cx, cam.cy - y0, cam.tan_fovx, cam.tan_fovy,
+                            cam.viewmat, cam.campos, cam.near_z)
 
     # first warm-up step: one full frame, which also sizes the band count so the
     # whole run stays within about 150 s
     t0 = time.perf_counter()
-    oracle.render(scene, cam, args.tile, 2, prec64=False)
+    oracle.render(scene, cam, args.tile, 2, prec64=False, omp=True)
     t_full = time.perf_counter() - t0
     extra_warmup = max(args.warmup - 1, 0)  # the full frame above counts as the first warm-up step
     steps = args.steps
@@ -266,30 +268,180 @@ def run_reference(args):
         y0 = b * bh
         c = band_cam(y0, min(bh, H - y0))
         t0 = time.perf_counter()
-        oracle.render(scene, c, args.tile, 2, prec64=False)
+        oracle.render(scene, c, args.tile, 2, prec64=False, omp=True)
         dt = time.perf_counter() - t0
         if s >= extra_warmup:
             times.append(dt)
     mean_band = sum(times) / len(times)
     fps = 1.0 / (bands * mean_band)
-    sample = (f"CPU oracle (FP32, single thread), AccuTile, {args.n} Gaussians; each step renders one of {bands} "
-              f"horizontal bands ({cam.width}x{bh}) of the {cam.width}x{H} frame through the whole pipeline "
-              f"(every Gaussian preprocessed per band); first full frame took {t_full:.2f} s")
+    sample = (f"CPU oracle (FP32, OpenMP over Gaussians and pixel rows, {cores} host threads), AccuTile, "
+              f"{args.n} Gaussians; each step renders one of {bands} horizontal band(s) ({cam.width}x{bh}) of the "
+              f"{cam.width}x{H} frame through the whole pipeline (every Gaussian preprocessed per band); first full "
+              f"frame took {t_full:.2f} s")
     emit({"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": args.gpus,
           "steps": steps, "warmup": args.warmup, "ms_per_step": mean_band * 1e3,
           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-          "config": {"workload": WORKLOAD, "gaussians": args.n, "width": cam.width, "height": H, "tile": args.tile,
-                     "mode": "accutile", "l2": "inputs exceed L2"},
-          "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": sample},
+          "config": config_dict(args, cam),
+          "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": sample},
           "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
 
 
 # ---------------------------------------------------------------- our arm
+def config_dict(args, cam):
+    """The workload description both arms print (identical by construction)."""
+    return {"workload": WORKLOAD, "gaussians": args.n, "width": cam.width, "height": cam.height, "tile": args.tile,
+            "mode": "accutile", "l2": "inputs exceed L2 (708 MB scene), no flush",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+class ModeTimer:
+    """Frames of one scene and camera in every tile mode, timed with CUDA
+    events on the context's stream (forward, per stage, CUDA-graph replay)."""
+
+    STAGES = ["preprocess", "intersect", "sort", "tile_ranges", "render"]
+
+    def __init__(self, raster, renderer, scene, cam, tile, modes, barrier, max_over_ranks, world):
+        self.raster, self.renderer, self.rast = raster, renderer, renderer.rast
+        self.scene, self.cam, self.tile = scene, cam, tile
+        self.barrier, self.max_over_ranks, self.world = barrier, max_over_ranks, world
+        self.frames, self.keys = {}, {}
+        for m in modes:  # size each mode's frame (one synchronising render)
+            out = renderer.render(scene, cam, m, tile)
+            self.keys[m] = out.num_keys
+            self.frames[m] = out.frame
+
+    def cfg(self, mode):
+        return self.raster.cfg_struct(self.tile, mode)
+
+    def check(self, mode):
+        K, flags = self.rast.gs_read_status(self.frames[mode], raise_on_error=False)
+        if flags:
+            raise RuntimeError(f"device status flags {flags} ({mode})")
+
+    def timed(self, mode, steps, warmup, sampler=None):
+        import torch
+
+        rast, cfg, f = self.rast, self.cfg(mode), self.frames[mode]
+        for _ in range(warmup):
+            rast.gs_forward(self.scene, self.cam, cfg, f)
+        self.barrier()
+        if sampler:
+            sampler.start()
+        l0 = rast.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(rast.stream)
+        for _ in range(steps):
+            rast.gs_forward(self.scene, self.cam, cfg, f)
+        e1.record(rast.stream)
+        launches = rast.launch_count() - l0  # kernels of the timed frames only
+        self.barrier()
+        if sampler:  # keep the same load running (untimed) until the sampler has >= 5 samples
+            t_end = time.time() + 2.0
+            while sampler.count() < 5 and time.time() < t_end:
+                for _ in range(20):
+                    rast.gs_forward(self.scene, self.cam, cfg, f)
+                torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        _, ms = replica_rate(steps, e0.elapsed_time(e1), self.world, self.max_over_ranks)
+        self.check(mode)
+        return ms, launches, clocks
+
+    def stages(self, mode, steps):
+        import torch
+
+        rast, cfg, f, scene, cam = self.rast, self.cfg(mode), self.frames[mode], self.scene, self.cam
+        calls = [lambda: rast.gs_preprocess(scene, cam, cfg, f), lambda: rast.gs_intersect(cam, cfg, f),
+                 lambda: rast.gs_sort(cam, cfg, f), lambda: rast.gs_tile_ranges(cam, cfg, f),
+                 lambda: rast.gs_render(cam, cfg, f)]
+        acc = [0.0] * 5
+        for _ in range(max(steps, 1)):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+            ev[0].record(rast.stream)
+            for k, c in enumerate(calls):
+                c()
+                ev[k + 1].record(rast.stream)
+            torch.cuda.synchronize()
+            for k in range(5):
+                acc[k] += ev[k].elapsed_time(ev[k + 1])
+        return {n: a / max(steps, 1) for n, a in zip(self.STAGES, acc)}
+
+    def graph(self, mode, steps):
+        """The same frame captured once as a CUDA graph and replayed."""
+        import torch
+
+        rast, cfg, f = self.rast, self.cfg(mode), self.frames[mode]
+        stream = rast.stream
+        side = torch.cuda.Stream(stream.device)
+        side.wait_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            rast.set_stream(side)
+            rast.gs_forward(self.scene, self.cam, cfg, f)
+            side.synchronize()
+            with torch.cuda.graph(g, stream=side):
+                rast.gs_forward(self.scene, self.cam, cfg, f)
+        rast.set_stream(stream)
+        stream.wait_stream(side)
+        for _ in range(3):
+            g.replay()
+        self.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            g.replay()
+        e1.record(stream)
+        self.barrier()
+        _, ms = replica_rate(steps, e0.elapsed_time(e1), self.world, self.max_over_ranks)
+        self.check(mode)
+        return ms
+
+    def table(self, steps, warmup, stage_steps):
+        """ms/frame, frames/s, K and per-stage ms of every mode."""
+        out = {}
+        for m in self.frames:
+            ms, _, _ = self.timed(m, steps, warmup)
+            out[m] = {"ms_per_frame": ms, "fps": 1e3 / ms, "keys": self.keys[m],
+                      "stages_ms": self.stages(m, stage_steps)}
+        return out
+
+    def image_diff(self, a, b):
+        """Pixels where mode a's and mode b's images differ, and the max |difference|."""
+        import torch
+
+        for m in (a, b):
+            self.rast.gs_forward(self.scene, self.cam, self.cfg(m), self.frames[m])
+        torch.cuda.synchronize()
+        d = (self.frames[a].image - self.frames[b].image).abs().amax(0)
+        return {"pixels_differing": int((d > 0).sum().item()), "max_abs_diff": float(d.max().item()),
+                "pixels": int(d.numel())}
+
+
+def stage_work(st, n, n_counted, K, sh_bytes, hw, tiles, passes):
+    """Algorithmic bytes per stage (the per-unit figures of the design notes
+    times the units of this frame)."""
+    return {
+        # geometry + opacity read and a 4 B count written for every Gaussian;
+        # SH read and the 48 B 2D state written for every counted one
+        "preprocess": n * (40 + 4) + n_counted * (sh_bytes + 48),
+        # counts read twice, 2D state read once per counted Gaussian, 12 B per key written
+        "intersect": n * 8 + n_counted * 48 + K * 12,
+        # lower bound: read and write every (key, value) pair once
+        "sort": K * 24,
+        # the onesweep design: one histogram read + 24 B per key and pass
+        "sort_design": K * 8 + K * 24 * passes,
+        "tile_ranges": K * 8 + tiles * 8,
+        # blend memory traffic: index + 48 B gathered per key, 20 B per pixel written
+        "render": K * (4 + 48) + hw * 20,
+    }
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2412_00578_gb300 import build, raster
+    from paper_2412_00578_gb300 import build, raster, synth
 
     world, rank, local = dist_env()
     if world > 1:
@@ -312,260 +464,95 @@ def run_ours(args):
 
     modes = [m for m in args.modes.split(",") if m]
     assert modes and modes[0] == "accutile", "the headline mode is accutile"
-    frames = {}
-    keys = {}
-    for m in modes:  # size each mode's frame (one synchronising render)
-        out = renderer.render(scene, cam, m, args.tile)
-        keys[m] = out.num_keys
-        frames[m] = out.frame
-
-    def timed(mode, steps, warmup, sampler=None):
-        cfg = raster.cfg_struct(args.tile, mode)
-        f = frames[mode]
-        for _ in range(warmup):
-            rast.gs_forward(scene, cam, cfg, f)
-        barrier()
-        if sampler:
-            sampler.start()
-        l0 = rast.launch_count()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            rast.gs_forward(scene, cam, cfg, f)
-        e1.record(stream)
-        launches = rast.launch_count() - l0  # kernels of the timed frames only
-        barrier()
-        if sampler:  # keep the same load running (untimed) until the sampler has >= 5 samples
-            t_end = time.time() + 2.0
-            while sampler.count() < 5 and time.time() < t_end:
-                for _ in range(20):
-                    rast.gs_forward(scene, cam, cfg, f)
-                torch.cuda.synchronize(dev)
-        clocks = sampler.stop() if sampler else None
-        _, ms = replica_rate(steps, e0.elapsed_time(e1), world, max_over_ranks)
-        K, flags = rast.gs_read_status(f, raise_on_error=False)
-        if flags:
-            raise RuntimeError(f"device status flags {flags} after timed loop ({mode})")
-        return ms, launches, clocks
-
-    def stage_breakdown(mode, steps):
-        cfg = raster.cfg_struct(args.tile, mode)
-        f = frames[mode]
-        names = ["preprocess", "intersect", "sort", "tile_ranges", "render"]
-        acc = [0.0] * 5
-        for _ in range(steps):
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-            ev[0].record(stream)
-            rast.gs_preprocess(scene, cam, cfg, f)
-            ev[1].record(stream)
-            rast.gs_intersect(cam, cfg, f)
-            ev[2].record(stream)
-            rast.gs_sort(cam, cfg, f)
-            ev[3].record(stream)
-            rast.gs_tile_ranges(cam, cfg, f)
-            ev[4].record(stream)
-            rast.gs_render(cam, cfg, f)
-            ev[5].record(stream)
-            torch.cuda.synchronize(dev)
-            for k in range(5):
-                acc[k] += ev[k].elapsed_time(ev[k + 1])
-        return {n: a / steps for n, a in zip(names, acc)}
-
-    bus = None
-    try:
-        props = torch.cuda.get_device_properties(dev)
-        bus = f"{props.pci_bus_id:02x}:{props.pci_device_id:02x}" if hasattr(props, "pci_bus_id") else None
-    except Exception:
-        bus = None
-
-    def timed_graph(mode, steps):
-        """The same frame captured once as a CUDA graph and replayed."""
-        cfg = raster.cfg_struct(args.tile, mode)
-        f = frames[mode]
-        side = torch.cuda.Stream(dev)
-        side.wait_stream(stream)
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.stream(side):
-            rast.set_stream(side)
-            rast.gs_forward(scene, cam, cfg, f)
-            side.synchronize()
-            with torch.cuda.graph(g, stream=side):
-                rast.gs_forward(scene, cam, cfg, f)
-        rast.set_stream(stream)
-        stream.wait_stream(side)
-        for _ in range(3):
-            g.replay()
-        barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            g.replay()
-        e1.record(stream)
-        barrier()
-        _, ms = replica_rate(steps, e0.elapsed_time(e1), world, max_over_ranks)
-        K, flags = rast.gs_read_status(f, raise_on_error=False)
-        if flags:
-            raise RuntimeError(f"device status flags {flags} after graph replays ({mode})")
-        return ms
+    T = ModeTimer(raster, renderer, scene, cam, args.tile, modes, barrier, max_over_ranks, world)
+    keys = T.keys
 
     # --- headline: AccuTile, K timed frames
     sampler = ClockSampler(None)
-    ms_acc, launches, clocks = timed("accutile", args.steps, args.warmup, sampler)
+    ms_acc, launches, clocks = T.timed("accutile", args.steps, args.warmup, sampler)
     per_mode = {"accutile": {"ms_per_frame": ms_acc, "fps": 1e3 / ms_acc, "keys": keys["accutile"]}}
-    ms_graph = timed_graph("accutile", args.steps)
-    per_mode["accutile"]["ms_per_frame_cuda_graph"] = ms_graph
+    per_mode["accutile"]["ms_per_frame_cuda_graph"] = T.graph("accutile", args.steps)
     for m in modes[1:]:
-        ms, _, _ = timed(m, max(10, args.steps // 2), args.warmup)
+        ms, _, _ = T.timed(m, max(10, args.steps // 2), args.warmup)
         per_mode[m] = {"ms_per_frame": ms, "fps": 1e3 / ms, "keys": keys[m]}
-    stages = {m: stage_breakdown(m, max(args.stage_steps, 1)) for m in modes} if args.stage_steps > 0 else {}
+    stages = {m: T.stages(m, args.stage_steps) for m in modes} if args.stage_steps > 0 else {}
+    diff_3sigma = T.image_diff("accutile", "3sigma") if "3sigma" in modes else None
 
-    # --- roofline of the dominant kernel (from the AccuTile stage breakdown)
+    # --- roofline: the dominant kernel (blend, the render stage) and the whole frame
     pk = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
     cfg_acc = raster.cfg_struct(args.tile, "accutile")
-    f_acc = frames["accutile"]
+    f_acc = T.frames["accutile"]
     rast.gs_forward(scene, cam, cfg_acc, f_acc)
     ev_pairs, contrib_pairs, exec_pairs = rast.gs_render_stats(cam, cfg_acc, f_acc)
-    counts = f_acc.counts[: scene.n]
-    n_counted = int((counts > 0).sum().item())
     n = scene.n
+    n_counted = int((f_acc.counts[:n] > 0).sum().item())
     K = keys["accutile"]
     hw = cam.width * cam.height
-    sh_bytes = 4 * 3 * (scene.sh_degree + 1) ** 2
-    st = stages["accutile"] if stages else stage_breakdown("accutile", 1)
-    stage_bytes = {
-        # geometry + opacity for all, SH + 48 B state for counted, 4 B count each
-        "preprocess": n * (40 + 4) + n_counted * (sh_bytes + 48),
-        # counts read twice, 2D state read once per counted Gaussian, 12 B per key written
-        "intersect": n * 8 + n_counted * 48 + K * 12,
-        # one histogram read (8 B/key) + per pass read and write of key and value (24 B/key)
-        "sort": K * 8 + K * 24 * raster_sort_passes(cam.width, cam.height, args.tile),
-        "tile_ranges": K * 8 + (cam.width // args.tile + 1) * (cam.height // args.tile + 1) * 8,
-        "render": K * (4 + 48) + hw * 20,
-    }
-    stage_frac = {k: {"ms": st[k], "gbs": stage_bytes[k] / (st[k] * 1e-3) / 1e9,
-                      "hbm_frac": stage_bytes[k] / (st[k] * 1e-3) / 1e9 / pk["hbm_gbs"]} for k in st}
-    # blend algorithmic work: 10 FP32 flops per evaluated pair (dx, dy, 2b dy, c dy dy,
-    # two fma, compare), 30 more per contributing pair (exp(-q/2) polynomial of 8 fma +
-    # reduction, alpha, T (1 - alpha), stop test, alpha T, 3 fma).
-    blend_flops = 10 * ev_pairs + 30 * contrib_pairs
-    sm_mhz = (clocks or {}).get("sm_mhz") or pk["sm_max_mhz"]
-    fp32_peak_tflops = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
-    dominant = max(st, key=st.get)
-    if dominant == "render":
-        achieved = blend_flops / (st["render"] * 1e-3) / 1e12
-        roof = {"kernel": "blend_kernel<16>", "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": blend_traffic(K),
-                "work": {"evaluated_pairs": ev_pairs, "contributing_pairs": contrib_pairs, "flops": blend_flops,
-                         "executed_pairs_after_culling": exec_pairs},
-                "peak_src": f"152 SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz"}
-    else:
-        achieved = stage_bytes[dominant] / (st[dominant] * 1e-3) / 1e9
-        roof = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_src": pk["src"]}
+    tiles = f_acc.gx * f_acc.gy
+    passes = raster_sort_passes(cam.width, cam.height, args.tile)
+    st = stages["accutile"] if stages else T.stages("accutile", 3)
+    work = stage_work(st, n, n_counted, K, 4 * 3 * (scene.sh_degree + 1) ** 2, hw, tiles, passes)
+    hbm = pk["hbm_gbs"]
+    stage_frac = {}
+    for k in T.STAGES:
+        gbs = work[k] / (st[k] * 1e-3) / 1e9
+        stage_frac[k] = {"ms": st[k], "algorithmic_bytes": work[k], "gbs": gbs, "hbm_frac": gbs / hbm}
+    stage_frac["sort"]["design_bytes"] = work["sort_design"]
+    stage_frac["sort"]["design_hbm_frac"] = work["sort_design"] / (st["sort"] * 1e-3) / 1e9 / hbm
+    # blend work per evaluated pair (dx, dy, 2b dy, c dy dy, two fma, compare):
+    # 8 flop; per contributing pair about 10 more (alpha, T (1 - alpha), stop
+    # test, alpha T, three colour fma) plus one exponential, counted apart
+    blend_flops = 8 * ev_pairs + 10 * contrib_pairs
+    fp32_peak = n_sm * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    achieved = blend_flops / (st["render"] * 1e-3) / 1e12
+    roof = {"kernel": f"blend_kernel<{args.tile}>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+            "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": blend_traffic(K),
+            "time_ms": st["render"], "time_src": "CUDA events around gs_render (the blend kernel alone)",
+            "work": {"evaluated_pairs": ev_pairs, "contributing_pairs": contrib_pairs, "flops": blend_flops,
+                     "flop_per_evaluated_pair": 8, "flop_per_contributing_pair": 10,
+                     "exp_evaluations": contrib_pairs, "executed_pairs_after_culling": exec_pairs},
+            "peak_src": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {pk['sm_max_mhz']:.0f} MHz (derived: "
+                        "MEASURED_PEAKS.json has no FP32 figure); of derived peak"}
+    # whole frame: the sum of the stages' lower-bound times over the frame time
+    lb_ms = {k: work[k] / (hbm * 1e9) * 1e3 for k in ("preprocess", "intersect", "sort", "tile_ranges")}
+    lb_ms["render"] = max(blend_flops / (fp32_peak * 1e12), work["render"] / (hbm * 1e9)) * 1e3
+    frame_roof = {"lower_bound_ms": lb_ms, "sum_lower_bound_ms": sum(lb_ms.values()), "ms_per_frame": ms_acc,
+                  "frac": sum(lb_ms.values()) / ms_acc,
+                  "how": "HBM stages: algorithmic bytes / measured copy bandwidth (sort: 24 B per key); "
+                         "blend: max(flops / FP32 peak, bytes / HBM)"}
 
     # --- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        host = {k: getattr(scene_cpu, k).pin_memory() for k in ("means", "scales", "rotations", "opacities", "sh")}
-        img_host = torch.empty(3, cam.height, cam.width, dtype=torch.float32).pin_memory()
-        h2d = sum(v.numel() * 4 for v in host.values())
-        d2h = img_host.numel() * 4
-        e2e_steps = min(args.steps, 20)
+        e2e = run_e2e(args, scene, scene_cpu, cam, rast, cfg_acc, f_acc, stream, barrier, max_over_ranks, world)
 
-        def e2e_step():
-            with torch.cuda.stream(stream):
-                for k, v in host.items():
-                    getattr(scene, k).copy_(v, non_blocking=True)
-            rast.gs_forward(scene, cam, cfg_acc, f_acc)
-            with torch.cuda.stream(stream):
-                img_host.copy_(f_acc.image, non_blocking=True)
-
-        for _ in range(3):
-            e2e_step()
-        barrier()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(e2e_steps):
-            e2e_step()
-        a1.record(stream)
-        barrier()
-        ms_serial = max_over_ranks(a0.elapsed_time(a1)) / e2e_steps
-
-        # Pipelined: two device copies of the scene; each step still uploads its
-        # whole scene and reads back its image, but step i+1's upload (on a copy
-        # stream) overlaps step i's render.
-        from paper_2412_00578_gb300 import synth as _synth
-
-        fields = ("means", "scales", "rotations", "opacities", "sh")
-        bufs = [scene, _synth.Scene(*[torch.empty_like(getattr(scene, k)) for k in fields], scene.sh_degree)]
-        cstream = torch.cuda.Stream(dev)
-        copied = [torch.cuda.Event(), torch.cuda.Event()]
-        released = [torch.cuda.Event(), torch.cuda.Event()]
-        for ev in released:
-            ev.record(stream)
-
-        def pipe_step(i):
-            b = i % 2
-            cstream.wait_event(released[b])
-            with torch.cuda.stream(cstream):
-                for k, v in host.items():
-                    getattr(bufs[b], k).copy_(v, non_blocking=True)
-            copied[b].record(cstream)
-            stream.wait_event(copied[b])
-            rast.gs_forward(bufs[b], cam, cfg_acc, f_acc)
-            with torch.cuda.stream(stream):
-                img_host.copy_(f_acc.image, non_blocking=True)
-            released[b].record(stream)
-
-        for i in range(3):
-            pipe_step(i)
-        barrier()
-        a0.record(stream)
-        cstream.wait_event(a0)
-        for i in range(e2e_steps):
-            pipe_step(i)
-        a1.record(stream)
-        barrier()
-        ms_e2e = max_over_ranks(a0.elapsed_time(a1)) / e2e_steps
-        e2e = {"value": world * 1e3 / ms_e2e, "unit": "frames/s", "ms_per_frame": ms_e2e,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "path": "per step: pinned host scene -> device copy (copy stream, into one of two device buffers), "
-                       "gs_forward, image -> pinned host; step i+1's copy overlaps step i's render",
-               "ms_per_frame_serial": ms_serial,
-               "serial_path": "the same steps with no overlap (copy, render, read back in order on one stream)",
-               "h2d_link_note": "host-to-device measured at about 211 GB/s on this box, so the 708 MB upload "
-                                "(3.35 ms) bounds the pipelined rate"}
-
-    # --- backward of the same frame: render backward, preprocess backward and
-    # the pruning score, alone and after its forward
     backward = None
     if not args.no_backward:
         backward = run_backward(args, raster, rast, scene, cam, cfg_acc, f_acc, stream, max_over_ranks, barrier)
 
-    # --- CPU oracle baseline (rank 0, N = 1 only)
+    # --- the other configurations: 16k box at 320x240 and the 300k prune, all modes
+    configs = None
+    if not args.no_configs:
+        configs = {}
+        box, box_cam = synth.small_box_workload()
+        Tb = ModeTimer(raster, raster.Renderer(dev), box.to(dev), box_cam, 16, modes, barrier, max_over_ranks, world)
+        configs["box-16k-320x240"] = Tb.table(max(20, args.steps), args.warmup, max(args.stage_steps, 3))
+        pr = synth.prune_random(scene_cpu, 300_000, seed=1).to(dev)
+        Tp = ModeTimer(raster, raster.Renderer(dev), pr, cam, args.tile, modes, barrier, max_over_ranks, world)
+        configs["outdoor-300k-prune-1280x840"] = Tp.table(max(20, args.steps), args.warmup, max(args.stage_steps, 3))
+        del Tb, Tp, pr
+
+    # --- CPU oracle baseline (rank 0, N = 1 only) and the FP64 error of the headline frame
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import oracle
+        cpu = run_cpu_baseline(args, scene_cpu, cam, f_acc)
 
-        oracle.build()
-        t0 = time.perf_counter()
-        ref = oracle.render(scene_cpu, cam, args.tile, 2, prec64=False)
-        dt = time.perf_counter() - t0
-        cpu = {"value": 1.0 / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
-               "sample": f"one full {cam.width}x{cam.height} AccuTile frame of the {n}-Gaussian scene, FP32 oracle, "
-                         f"single thread ({dt:.1f} s)"}
-        img = f_acc.image.cpu().numpy()
-        cpu["image_max_abs_err_vs_gpu"] = float(abs(img.astype("float64") - ref["image"]).max())
-
-    # --- multi-view: 64 orbit cameras of a 1.5M scene, autotuned, one CUDA graph
     multiview = None
     if not args.no_multiview:
         multiview = run_multiview(args, dev, max_over_ranks, barrier)
 
-    # --- serving: resident scenes, Poisson arrivals, continuous batching
     served = None
     if not args.no_serve and rank == 0:
         served = run_serving(args, dev, scene)
@@ -574,17 +561,139 @@ def run_ours(args):
         fps = world * 1e3 / ms_acc
         emit({"metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_acc, "higher_is_better": True, "scaling": "weak",
-              "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-              "config": {"workload": WORKLOAD, "gaussians": n, "width": cam.width, "height": cam.height,
-                         "tile": args.tile, "mode": "accutile", "l2": "inputs exceed L2 (708 MB scene), no flush",
-                         "parallelism": f"replicas x{world}"},
+              "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(args, cam),
               "ms_per_frame": ms_acc, "modes": per_mode,
               "speedup_vs_3sigma": (per_mode["3sigma"]["ms_per_frame"] / ms_acc) if "3sigma" in per_mode else None,
-              "stages_ms": stages, "stage_roofline": stage_frac,
+              "image_vs_3sigma": diff_3sigma,
+              "speedup_vs_snugbox": (per_mode["snugbox"]["ms_per_frame"] / ms_acc) if "snugbox" in per_mode else None,
+              "stages_ms": stages, "stage_roofline": stage_frac, "frame_roofline": frame_roof,
               "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
-              "cpu_baseline": cpu, "backward": backward, "multiview": multiview, "served": served})
+              "cpu_baseline": cpu, "backward": backward, "configs": configs, "multiview": multiview,
+              "served": served})
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_e2e(args, scene, scene_cpu, cam, rast, cfg, frame, stream, barrier, max_over_ranks, world):
+    """The same frame through the public API with the scene uploaded from
+    pinned host memory and the image read back every step."""
+    import torch
+
+    from paper_2412_00578_gb300 import synth
+
+    dev = scene.means.device
+    fields = ("means", "scales", "rotations", "opacities", "sh")
+    host = {k: getattr(scene_cpu, k).pin_memory() for k in fields}
+    img_host = torch.empty(3, cam.height, cam.width, dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * 4 for v in host.values())
+    d2h = img_host.numel() * 4
+    steps = min(args.steps, 20)
+
+    # the host-to-device link, measured here: the scene's upload alone
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for k, v in host.items():
+            getattr(scene, k).copy_(v, non_blocking=True)
+    barrier()
+    a0.record(stream)
+    for _ in range(3):
+        with torch.cuda.stream(stream):
+            for k, v in host.items():
+                getattr(scene, k).copy_(v, non_blocking=True)
+    a1.record(stream)
+    barrier()
+    h2d_gbs = 3 * h2d / (a0.elapsed_time(a1) * 1e-3) / 1e9
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            for k, v in host.items():
+                getattr(scene, k).copy_(v, non_blocking=True)
+        rast.gs_forward(scene, cam, cfg, frame)
+        with torch.cuda.stream(stream):
+            img_host.copy_(frame.image, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    barrier()
+    a0.record(stream)
+    for _ in range(steps):
+        e2e_step()
+    a1.record(stream)
+    barrier()
+    ms_serial = max_over_ranks(a0.elapsed_time(a1)) / steps
+
+    # Pipelined: two device copies of the scene; each step still uploads its
+    # whole scene and reads back its image, but step i+1's upload (on a copy
+    # stream) overlaps step i's render.
+    bufs = [scene, synth.Scene(*[torch.empty_like(getattr(scene, k)) for k in fields], scene.sh_degree)]
+    cstream = torch.cuda.Stream(dev)
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    released = [torch.cuda.Event(), torch.cuda.Event()]
+    for ev in released:
+        ev.record(stream)
+
+    def pipe_step(i):
+        b = i % 2
+        cstream.wait_event(released[b])
+        with torch.cuda.stream(cstream):
+            for k, v in host.items():
+                getattr(bufs[b], k).copy_(v, non_blocking=True)
+        copied[b].record(cstream)
+        stream.wait_event(copied[b])
+        rast.gs_forward(bufs[b], cam, cfg, frame)
+        with torch.cuda.stream(stream):
+            img_host.copy_(frame.image, non_blocking=True)
+        released[b].record(stream)
+
+    for i in range(3):
+        pipe_step(i)
+    barrier()
+    a0.record(stream)
+    cstream.wait_event(a0)
+    for i in range(steps):
+        pipe_step(i)
+    a1.record(stream)
+    barrier()
+    ms_e2e = max_over_ranks(a0.elapsed_time(a1)) / steps
+    return {"value": world * 1e3 / ms_e2e, "unit": "frames/s", "ms_per_frame": ms_e2e,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "path": "per step: pinned host scene -> device copy (copy stream, into one of two device buffers), "
+                    "gs_forward, image -> pinned host; step i+1's copy overlaps step i's render",
+            "ms_per_frame_serial": ms_serial,
+            "serial_path": "the same steps with no overlap (copy, render, read back in order on one stream)",
+            "h2d_gbs_measured": h2d_gbs,
+            "h2d_bound_ms": h2d / (h2d_gbs * 1e9) * 1e3}
+
+
+def run_cpu_baseline(args, scene_cpu, cam, f_acc):
+    """The oracle timed on the host cores: all cores (OpenMP build of the same
+    code) and one thread, FP32, AccuTile, the full headline frame; and the FP64
+    oracle's image error of the GPU frame beside the FP32 parity."""
+    import oracle
+
+    oracle.build()
+    oracle.build(omp=True)
+    cores = os.cpu_count() or 1
+    img = f_acc.image.cpu().numpy().astype("float64")
+    t0 = time.perf_counter()
+    ref = oracle.render(scene_cpu, cam, args.tile, 2, prec64=False)
+    t_single = time.perf_counter() - t0
+    frames = 3
+    t0 = time.perf_counter()
+    for _ in range(frames):
+        ref_omp = oracle.render(scene_cpu, cam, args.tile, 2, prec64=False, omp=True)
+    t_omp = (time.perf_counter() - t0) / frames
+    ref64 = oracle.render(scene_cpu, cam, args.tile, 2, prec64=True, omp=True)
+    return {"value": 1.0 / t_omp, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": f"{frames} full {cam.width}x{cam.height} AccuTile frames of the {args.n}-Gaussian scene, FP32 "
+                      f"oracle built with OpenMP over Gaussians and pixel rows on {cores} host threads "
+                      f"({t_omp:.2f} s per frame)",
+            "single_thread": {"value": 1.0 / t_single, "unit": "frames/s", "cores": 1,
+                              "sample": f"one full frame, same oracle without OpenMP ({t_single:.2f} s)"},
+            "image_max_abs_err_vs_gpu": float(abs(img - ref["image"]).max()),
+            "image_max_abs_err_omp_vs_gpu": float(abs(img - ref_omp["image"]).max()),
+            "image_max_abs_err_gpu_vs_fp64_oracle": float(abs(img - ref64["image"]).max())}
 
 
 def run_backward(args, raster, rast, scene, cam, cfg, frame, stream, max_over_ranks, barrier):

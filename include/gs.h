@@ -98,7 +98,8 @@ typedef struct gs_raster_cfg {
 } gs_raster_cfg;
 
 /* Per-frame buffers, all device memory owned by the caller, sized by
- * gs_frame_sizes() for (n_capacity, width, height, tile, key_capacity).
+ * gs_frame_sizes() for (n_capacity, width, height, tile, key_capacity);
+ * zero-fill scratch once after allocating it (see gs_read_culled).
  * Layouts:
  *   proj     [3][n_capacity][4] float: plane 0 = (u, v, opacity, depth),
  *            plane 1 = conic (a, b, c) and t = 2 log(255 sigma),
@@ -180,16 +181,18 @@ gs_status gs_intersect(gs_context* ctx, const gs_camera* cam, const gs_raster_cf
 gs_status gs_sort(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame);
 
 /* identifyTileRanges (Sec. 3.2.2): ranges[tile] = [start, end) of the tile's
- * entries in the sorted keys; [0, 0) for empty tiles. */
+ * entries in the sorted keys; [0, 0) for empty tiles.  Also records, in
+ * frame->scratch, the order in which gs_render launches the tiles (heaviest
+ * first; frames of up to 32768 tiles). */
 gs_status gs_tile_ranges(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame);
 
 /* render (Sec. 3.2.3, Eqs. render_alpha, 2d_gaussian_scalar, contribution):
  * for each pixel, walk its tile's Gaussians front to back; a Gaussian counts
  * where q <= t (alpha >= 1/255), alpha = min(0.99, sigma exp(-q/2)); stop
  * before a Gaussian that would bring the transmittance below 1e-4; finally
- * add T * bg.  Writes image, final_T and last.  Tiles are processed heaviest
- * first (their launch order is kept in frame->scratch); the order does not
- * change any output. */
+ * add T * bg.  Writes image, final_T and last.  Tiles are processed in the
+ * order the frame's last gs_tile_ranges recorded (heaviest first); the order
+ * does not change any output.  Requires gs_tile_ranges on the sorted keys. */
 gs_status gs_render(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame);
 
 /* Instrumented render: the same blend as gs_render (same outputs), which
@@ -324,8 +327,29 @@ gs_status gs_batch_status(gs_context* ctx, const gs_batch_frame* frame, int64_t*
 
 /* Synchronise the stream and read the frame's device status: the key total
  * K and the GS_FLAG_* bits (both host outputs, nullable).  Returns
- * GS_ERR_CAPACITY or GS_ERR_TIMEOUT if the corresponding flag is set. */
+ * GS_ERR_CAPACITY or GS_ERR_TIMEOUT if the corresponding flag is set.
+ * After GS_FLAG_TIMEOUT the frame holds no keys for the later sort passes,
+ * gs_tile_ranges and gs_render (the image is the background); the context
+ * stays usable and the next frame starts afresh. */
 gs_status gs_read_status(gs_context* ctx, const gs_frame* frame, int64_t* num_keys, uint32_t* flags);
+
+/* Synchronise and read how many Gaussians the frame's last gs_preprocess
+ * culled because a parameter was NaN or infinite or the quaternion was zero
+ * (*culled, host).  The count is taken over by gs_intersect, so read it after
+ * that call.  Its first value after the scratch buffer was allocated is
+ * valid only if the buffer was zero-filled once (the library keeps the word
+ * consistent afterwards). */
+gs_status gs_read_culled(gs_context* ctx, const gs_frame* frame, int64_t* culled);
+
+/* Failure detection of the sort's bounded waits.  Each decoupled look-back
+ * wait of gs_sort gives up after max_polls polls (0 = the default, 4,194,304,
+ * far beyond any wait of a correct run) and then sets GS_FLAG_TIMEOUT.  If
+ * withhold_partition >= 0, that key partition (4096 keys) of every sort pass
+ * never publishes its digit counts, so the wait of the partition after it
+ * must run out: a test uses this, with a small max_polls, to exercise the
+ * timeout path without any fault.  -1 restores normal publishing.  Applies
+ * to later gs_sort / gs_forward / gs_forward_batch calls on this context. */
+gs_status gs_set_sort_wait(gs_context* ctx, uint32_t max_polls, int64_t withhold_partition);
 
 #ifdef __cplusplus
 }

@@ -25,28 +25,38 @@ import numpy as np
 _HERE = Path(__file__).resolve().parent
 _SRC = _HERE / "oracle.cpp"
 _OUT = _HERE / "_build" / "liboracle.so"
+_OUT_OMP = _HERE / "_build" / "liboracle_omp.so"
 CXXFLAGS = ["-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
 
 MODES = {"3sigma": 0, "snugbox": 1, "accutile": 2}
 
 
-def build(force: bool = False) -> Path:
-    """Compile ``oracle.cpp`` into ``_build/liboracle.so`` with g++ (FP contraction off)."""
-    if not force and _OUT.exists() and _OUT.stat().st_mtime >= _SRC.stat().st_mtime:
-        return _OUT
-    _OUT.parent.mkdir(parents=True, exist_ok=True)
-    tmp = _OUT.with_suffix(f".{os.getpid()}.tmp")
-    cmd = [os.environ.get("CXX", "g++"), *CXXFLAGS, str(_SRC), "-o", str(tmp)]
+def build(force: bool = False, omp: bool = False) -> Path:
+    """Compile ``oracle.cpp`` into ``_build/liboracle.so`` with g++ (FP
+    contraction off); with ``omp`` also into ``_build/liboracle_omp.so``
+    (-fopenmp: the same code with its independent loops on all host cores)."""
+    out = _OUT_OMP if omp else _OUT
+    if not force and out.exists() and out.stat().st_mtime >= _SRC.stat().st_mtime:
+        return out
+    out.parent.mkdir(parents=True, exist_ok=True)
+    tmp = out.with_suffix(f".{os.getpid()}.tmp")
+    cmd = [os.environ.get("CXX", "g++"), *CXXFLAGS, *(["-fopenmp"] if omp else []), str(_SRC), "-o", str(tmp)]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _OUT)
-    return _OUT
+    os.replace(tmp, out)
+    return out
 
 
 _lib = None
+_lib_omp = None
 
 
-def lib() -> ctypes.CDLL:
-    global _lib
+def lib(omp: bool = False) -> ctypes.CDLL:
+    global _lib, _lib_omp
+    if omp:
+        if _lib_omp is None:
+            _lib_omp = ctypes.CDLL(str(build(omp=True)))
+            _declare(_lib_omp)
+        return _lib_omp
     if _lib is None:
         _lib = ctypes.CDLL(str(build()))
         _declare(_lib)
@@ -130,13 +140,13 @@ PROJ_FIELDS = ["u", "v", "depth", "opacity", "a", "b", "c", "t", "r", "g", "b_",
                "radius", "valid"]
 
 
-def preprocess(scene, cam, tile: int = 16, mode: int = 2, prec64: bool = True):
+def preprocess(scene, cam, tile: int = 16, mode: int = 2, prec64: bool = True, omp: bool = False):
     """Returns (state[n,16] in PROJ_FIELDS order, counts[n] int64)."""
     n, (m, s, r, o, sh), deg = _scene_arrays(scene)
     w, h, cf = _cam(cam)
     out = np.zeros((n, 16), np.float64)
     counts = np.zeros(n, np.int64)
-    lib().oracle_preprocess(int(prec64), n, _ptr(m), _ptr(s), _ptr(r), _ptr(o), _ptr(sh), deg, w, h, _ptr(cf),
+    lib(omp).oracle_preprocess(int(prec64), n, _ptr(m), _ptr(s), _ptr(r), _ptr(o), _ptr(sh), deg, w, h, _ptr(cf),
                             tile, mode, _ptr(out), _ptr(counts))
     return out, counts
 
@@ -168,11 +178,12 @@ def exact_tile_mask(e, tile: int, gx: int, gy: int) -> np.ndarray:
 
 
 # ------------------------------------------------------------------ pipelines
-def count_keys(scene, cam, tile: int, mode: int, prec64: bool = False) -> int:
-    return int(preprocess(scene, cam, tile, mode, prec64)[1].sum())
+def count_keys(scene, cam, tile: int, mode: int, prec64: bool = False, omp: bool = False) -> int:
+    return int(preprocess(scene, cam, tile, mode, prec64, omp)[1].sum())
 
 
-def render(scene, cam, tile: int = 16, mode: int = 2, bg=(0.0, 0.0, 0.0), prec64: bool = False, key_cap=None):
+def render(scene, cam, tile: int = 16, mode: int = 2, bg=(0.0, 0.0, 0.0), prec64: bool = False, key_cap=None,
+           omp: bool = False):
     """Full forward pipeline of one tile mode.  Returns a dict with the
     unsorted and sorted (key, id) lists, tile ranges, image (3,H,W), final T
     and last-contributor index, all as numpy arrays, and the blend's pair
@@ -183,7 +194,7 @@ def render(scene, cam, tile: int = 16, mode: int = 2, bg=(0.0, 0.0, 0.0), prec64
     gx, gy = grid(w, h, tile)
     bgv = np.asarray(bg, np.float32)
     if key_cap is None:
-        key_cap = count_keys(scene, cam, tile, mode, prec64)
+        key_cap = count_keys(scene, cam, tile, mode, prec64, omp)
     key_cap = max(int(key_cap), 1)
     ku = np.zeros(key_cap, np.uint64)
     vu = np.zeros(key_cap, np.uint32)
@@ -195,7 +206,7 @@ def render(scene, cam, tile: int = 16, mode: int = 2, bg=(0.0, 0.0, 0.0), prec64
     T = np.zeros((h, w), np.float64)
     last = np.zeros((h, w), np.uint32)
     pairs = np.zeros(2, np.int64)
-    rc = lib().oracle_render(int(prec64), n, _ptr(m), _ptr(s), _ptr(r), _ptr(o), _ptr(sh), deg, w, h, _ptr(cf), tile,
+    rc = lib(omp).oracle_render(int(prec64), n, _ptr(m), _ptr(s), _ptr(r), _ptr(o), _ptr(sh), deg, w, h, _ptr(cf), tile,
                              mode, _ptr(bgv), key_cap, _ptr(ku), _ptr(vu), _ptr(ks), _ptr(vs), _ptr(nk),
                              _ptr(ranges), _ptr(img), _ptr(T), _ptr(last), _ptr(pairs))
     K = int(nk[0])

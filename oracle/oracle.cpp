@@ -565,8 +565,11 @@ bool blend_step(Pixel<R>& px, const Proj<R>& P, R pxf, R pyf, uint32_t pos) {
 }
 
 // ---------------------------------------------------------------- pipelines
+// (With -fopenmp the independent per-Gaussian and per-pixel-row loops below
+// run on all host cores; the arithmetic and every result are the same.)
 template <typename R> std::vector<Proj<R>> preprocess_all(const SceneIn& s, const Cam<R>& cam) {
     std::vector<Proj<R>> out(static_cast<size_t>(s.n));
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < s.n; ++i) out[i] = preprocess_one<R>(s, i, cam);
     return out;
 }
@@ -629,6 +632,7 @@ int render_impl(const SceneIn& s, int width, int height, const float* camf, int 
     // including the one that stops the pixel) and the pairs that add colour.
     const int64_t HW = int64_t(width) * height;
     int64_t evaluated = 0, contributed = 0;
+#pragma omp parallel for schedule(dynamic, 2) reduction(+ : evaluated, contributed)
     for (int py = 0; py < height; ++py) {
         for (int px = 0; px < width; ++px) {
             int64_t tid = int64_t(py / tile) * g.gx + (px / tile);
@@ -993,6 +997,7 @@ void oracle_preprocess(int prec64, int64_t n, const float* means, const float* s
     auto noop = [](int, int) {};
     if (prec64) {
         Cam<double> cam = make_cam<double>(width, height, camf);
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) {
             Proj<double> P = preprocess_one<double>(s, i, cam);
             pack_proj(P, out + 16 * i);
@@ -1000,6 +1005,7 @@ void oracle_preprocess(int prec64, int64_t n, const float* means, const float* s
         }
     } else {
         Cam<float> cam = make_cam<float>(width, height, camf);
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) {
             Proj<float> P = preprocess_one<float>(s, i, cam);
             pack_proj(P, out + 16 * i);

@@ -44,6 +44,8 @@ ScratchLayout scratch_layout(int64_t ncap, int64_t kcap) {
     off += align_up(kSortCtlWords * 4);
     L.lookback = off;
     off += align_up(2 * std::max<int64_t>(sort_partitions_for(kcap), 1) * 256 * 4);
+    L.order = off;
+    off += align_up((int64_t)kMaxOrderedTiles * 4);
     L.total = off;
     return L;
 }
@@ -117,6 +119,7 @@ bool make_view(gs_context* ctx, const gs_frame* f, FrameView* v, unsigned need) 
     v->sort_ticket = v->sort_hist + kMaxPasses * 256;
     v->sort_lookback = reinterpret_cast<uint32_t*>(s + L.lookback);
     v->sort_partitions = std::max<int64_t>(sort_partitions_for(f->key_capacity), 1);
+    v->tile_order = reinterpret_cast<uint32_t*>(s + L.order);
     if ((reinterpret_cast<uintptr_t>(f->proj) & 15) || (reinterpret_cast<uintptr_t>(f->keys) & 7) ||
         (reinterpret_cast<uintptr_t>(f->ranges) & 7) || (reinterpret_cast<uintptr_t>(f->scratch) & 15)) {
         set_error(ctx, GS_ERR_INVALID, "frame buffer misaligned (proj/scratch need 16 B, keys/ranges 8 B)");
@@ -298,6 +301,27 @@ gs_status gs_render_backward(gs_context* ctx, const gs_scene* scene, const gs_ca
                          !grads->scales || !grads->rotations || !grads->opacities || !grads->sh))
         return set_error(ctx, GS_ERR_INVALID, "scene or grads has a NULL array");
     return launch_backward(ctx, scene, cam, cfg, v, dL_dimage, grads);
+}
+
+gs_status gs_set_sort_wait(gs_context* ctx, uint32_t max_polls, int64_t withhold_partition) {
+    if (!ctx) return GS_ERR_INVALID;
+    ctx->sort_spin_limit = max_polls ? max_polls : kDefaultSpinLimit;
+    ctx->sort_withhold = withhold_partition < 0 ? -1 : withhold_partition;
+    return GS_OK;
+}
+
+gs_status gs_read_culled(gs_context* ctx, const gs_frame* frame, int64_t* culled) {
+    gs_status st = enter(ctx);
+    if (st) return st;
+    if (!culled) return set_error(ctx, GS_ERR_INVALID, "culled is NULL");
+    FrameView v;
+    if (!make_view(ctx, frame, &v)) return GS_ERR_INVALID;
+    uint32_t w = 0;
+    cudaError_t e = cudaMemcpyAsync(&w, v.status + kStatusCulled, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return set_error(ctx, GS_ERR_CUDA, "read_culled: %s", cudaGetErrorString(e));
+    *culled = (int64_t)w;
+    return GS_OK;
 }
 
 gs_status gs_read_status(gs_context* ctx, const gs_frame* frame, int64_t* num_keys, uint32_t* flags) {

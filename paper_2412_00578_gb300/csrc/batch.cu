@@ -124,6 +124,7 @@ bool make_batch_view(gs_context* ctx, const gs_batch_frame* f, int num_cams, Fra
     v->sort_ticket = v->sort_hist + kMaxPasses * 256;
     v->sort_lookback = reinterpret_cast<uint32_t*>(s + L.base.lookback);
     v->sort_partitions = std::max<int64_t>(sort_partitions_for(f->key_capacity), 1);
+    v->tile_order = reinterpret_cast<uint32_t*>(s + L.base.order);
     v->table = reinterpret_cast<const CamRec*>(s + L.table);
     v->num_cams = num_cams;
     v->cam_stride = f->n_capacity;
@@ -199,9 +200,9 @@ gs_status gs_batch_status(gs_context* ctx, const gs_batch_frame* frame, int64_t*
     FrameView v;
     if (!make_batch_view(ctx, frame, 1, &v)) return GS_ERR_INVALID;
     uint32_t w[4] = {0, 0, 0, 0};
-    if (cudaMemcpyAsync(w, v.status, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
-        cudaStreamSynchronize(ctx->stream) != cudaSuccess)
-        return set_error(ctx, GS_ERR_CUDA, "batch_status: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaError_t e = cudaMemcpyAsync(w, v.status, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return set_error(ctx, GS_ERR_CUDA, "batch_status: %s", cudaGetErrorString(e));
     const int64_t K = (int64_t)w[0] | ((int64_t)w[1] << 32);
     if (num_keys) *num_keys = K;
     const uint32_t fl = w[2] | w[3];

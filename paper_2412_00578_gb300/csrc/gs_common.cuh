@@ -25,7 +25,15 @@ constexpr int kMaxTile = 32;
 //   [0] key total K, low 32 bits   [1] K high bits   [2] GS_FLAG_* bits
 //   [3] multi-view set-up flags (GS_FLAG_BATCH), written by every batch set-up
 //   [4..9] three 64-bit counters of the instrumented blend (gs_render_stats)
+//   [10] Gaussians culled by the running preprocess for non-finite
+//        parameters or a zero quaternion (accumulated, then moved to [11] and
+//        cleared by the scan that follows it)
+//   [11] that count for the last preprocessed frame
 constexpr int kStatusWords = 16;
+constexpr int kStatusCulledAcc = 10;
+constexpr int kStatusCulled = 11;
+// Bound of one sort look-back wait, in polls (about 32 ns apart).
+constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 
 // Camera constants as the kernels use them.
 struct CamK {
@@ -65,6 +73,7 @@ struct FrameView {
     uint32_t* sort_ticket;     // [kMaxPasses]
     uint32_t* sort_lookback;   // [2][sort_partitions][256] look-back words, see sort.cu
     int64_t sort_partitions;   // partitions the look-back table holds
+    uint32_t* tile_order;      // [kMaxOrderedTiles] the blend's tile launch order
     // multi-view batches only (table == nullptr for a single camera)
     const CamRec* table = nullptr;
     int num_cams = 1;
@@ -221,6 +230,8 @@ struct gs_context {
     cudaStream_t stream = nullptr;
     int num_sms = 0;
     int64_t launches = 0;
+    uint32_t sort_spin_limit = gs::kDefaultSpinLimit;  // gs_set_sort_wait
+    int64_t sort_withhold = -1;                        // gs_set_sort_wait: partition that does not publish
     char err[512] = {0};
 };
 
@@ -236,8 +247,10 @@ int sort_tile_bits(int64_t tiles);
 void sort_plan(int64_t tiles, int digit_override, int* passes, int* digit_bits);
 
 struct ScratchLayout {
-    int64_t status, partials, hist, lookback, total;
+    int64_t status, partials, hist, lookback, order, total;
 };
+// Frames with more tiles than this blend them in index order.
+constexpr unsigned kMaxOrderedTiles = 1u << 15;
 ScratchLayout scratch_layout(int64_t ncap, int64_t kcap);
 int64_t sort_partitions_for(int64_t kcap);
 int64_t scan_blocks_for(int64_t n);
@@ -247,10 +260,9 @@ gs_status launch_preprocess(gs_context* ctx, const gs_scene* s, const gs_camera*
                             const FrameView& v);
 gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v);
 gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override = 0);
+// identifyTileRanges, then the blend's heaviest-first tile launch order
+// (for frames of at most kMaxOrderedTiles tiles).
 gs_status launch_ranges(gs_context* ctx, const FrameView& v);
-// Heaviest-first launch order of the tiles (kept in the idle sort look-back
-// table), or nullptr when the tiles do not fit it (then CTA = tile).
-const uint32_t* launch_tile_order(gs_context* ctx, const FrameView& v);
 gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v,
                         unsigned long long* stats = nullptr);
 gs_status launch_backward(gs_context* ctx, const gs_scene* s, const gs_camera* cam, const gs_raster_cfg* cfg,

@@ -92,7 +92,13 @@ __global__ void __launch_bounds__(1024) scan_top_kernel(long long* __restrict__ 
         status[0] = (uint32_t)(K & 0xffffffffll);
         status[1] = (uint32_t)(K >> 32);
         status[2] = K > kcap ? GS_FLAG_CAPACITY : 0u;
-        if (clear3) status[3] = 0u;
+        if (clear3) {
+            status[3] = 0u;
+            // the preprocess that produced these counts has completed: keep
+            // its culled count and start the next frame's at zero
+            status[kStatusCulled] = status[kStatusCulledAcc];
+            status[kStatusCulledAcc] = 0u;
+        }
     }
 }
 

@@ -30,6 +30,7 @@ struct PreArgs {
     int32_t* counts;
     const CamRec* table;  // multi-view: per-camera constants (else nullptr)
     int num_cams;
+    uint32_t* culled;     // count of non-finite / zero-quaternion Gaussians (nullable)
 };
 
 // Real SH normalisation constants, from their closed forms:
@@ -111,8 +112,9 @@ __device__ __forceinline__ void preprocess_one(const PreArgs& A, const CamK& C, 
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(A.sh + (int64_t)k * n + i));
             }
         }
-        ok = ok && (pz > C.near_z);
         const float n2 = ((qw * qw + qx * qx) + qy * qy) + qz * qz;
+        if (A.culled && !(ok && n2 > 0.0f)) atomicAdd(A.culled, 1u);  // rare: no aggregation
+        ok = ok && (pz > C.near_z);
         ok = ok && (n2 > 0.0f);
         if (ok) {
             // quotients by one denominator are products with its reciprocal
@@ -274,6 +276,7 @@ gs_status launch_preprocess(gs_context* ctx, const gs_scene* s, const gs_camera*
     A.counts = v.counts;
     A.table = v.table;
     A.num_cams = v.num_cams;
+    A.culled = v.table ? nullptr : v.status + kStatusCulledAcc;
     const int threads = 256;
     if (v.table) {
         A.ncap = v.cam_stride;

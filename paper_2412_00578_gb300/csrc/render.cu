@@ -25,9 +25,10 @@
 namespace gs {
 namespace {
 
-// Keys present in the buffer (see sort.cu): none when the emit was skipped.
+// Keys present in the buffer (see sort.cu): none when the emit was skipped
+// or a sort wait gave up.
 __device__ __forceinline__ uint32_t frame_keys_r(const uint32_t* status) {
-    return ((status[2] & GS_FLAG_CAPACITY) || status[3]) ? 0u : status[0];
+    return ((status[2] & (GS_FLAG_CAPACITY | GS_FLAG_TIMEOUT)) || status[3]) ? 0u : status[0];
 }
 
 // Four consecutive keys per thread (two 16-byte loads when the buffer is
@@ -69,8 +70,6 @@ __global__ void __launch_bounds__(256) ranges_kernel(const uint64_t* __restrict_
     }
 }
 
-constexpr unsigned kMaxOrderedTiles = 1u << 15;  // beyond this the blend runs tiles in index order
-
 struct BlendArgs {
     const uint2* ranges;
     const uint32_t* vals;
@@ -88,6 +87,7 @@ struct BlendArgs {
     int64_t cam_stride;
     int64_t pixel_capacity;
     const uint32_t* order;      // tile of each CTA (heaviest first), or nullptr for tile = CTA
+    unsigned tiles;             // CTAs launched (tiles of the frame, or the batch's tile capacity)
 };
 
 // Camera owning global tile g of a multi-view batch: the last camera whose
@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 4 : 16)) blend_
     __shared__ uint32_t s_mask[NB];
     __shared__ uint32_t s_pass[NT / 32][NB / 32][32];  // per warp, chunk, lane: passing entries
     const int tile = A.order ? (int)A.order[blockIdx.x] : (int)blockIdx.x;  // global tile index
+    if ((unsigned)tile >= A.tiles) return;  // an order never written by gs_tile_ranges
     int gx = A.gx, width = A.width, height = A.height, local = tile;
     float* image = A.image;
     float* final_T = A.final_T;
@@ -343,21 +344,19 @@ gs_status launch_ranges(gs_context* ctx, const FrameView& v) {
     (void)launch_pdl(ctx->stream, zero_words_kernel, dim3(zero_blocks(2 * (int64_t)tiles)), dim3(256), 0,
                      reinterpret_cast<uint32_t*>(v.ranges), 2 * (int64_t)tiles);
     ctx->launches += 1;
-    if (v.kcap == 0) return GS_OK;
-    const int64_t blocks = (v.kcap + 1023) / 1024;  // 4 keys per thread
-    (void)launch_pdl(ctx->stream, ranges_kernel, dim3((unsigned)blocks), dim3(256), 0, v.keys0, v.status, v.ranges);
-    ctx->launches += 1;
+    if (v.kcap > 0) {
+        const int64_t blocks = (v.kcap + 1023) / 1024;  // 4 keys per thread
+        (void)launch_pdl(ctx->stream, ranges_kernel, dim3((unsigned)blocks), dim3(256), 0, v.keys0, v.status,
+                         v.ranges);
+        ctx->launches += 1;
+    }
+    // the blend's launch order, from the ranges just found
+    if (tiles > 0 && tiles <= kMaxOrderedTiles) {
+        (void)launch_pdl(ctx->stream, tile_order_kernel, dim3(1), dim3(1024), 0, v.ranges, (uint32_t)tiles,
+                         v.tile_order);
+        ctx->launches += 1;
+    }
     return check_launch(ctx, "tile_ranges");
-}
-
-const uint32_t* launch_tile_order(gs_context* ctx, const FrameView& v) {
-    // The order array lives in the sort's look-back table, idle until the next
-    // sort, which clears every word of it that it reads before reading it.
-    const unsigned tiles = (unsigned)(v.gx * v.gy);
-    if (tiles == 0 || tiles > kMaxOrderedTiles || (int64_t)tiles > 2 * v.sort_partitions * 256) return nullptr;
-    (void)launch_pdl(ctx->stream, tile_order_kernel, dim3(1), dim3(1024), 0, v.ranges, tiles, v.sort_lookback);
-    ctx->launches += 1;
-    return v.sort_lookback;
 }
 
 gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v, unsigned long long* stats) {
@@ -383,7 +382,8 @@ gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameVi
     A.pixel_capacity = v.pixel_capacity;
     const unsigned tiles = (unsigned)(v.gx * v.gy);
     if (tiles == 0) return GS_OK;
-    A.order = launch_tile_order(ctx, v);
+    A.order = tiles <= kMaxOrderedTiles ? v.tile_order : nullptr;  // written by launch_ranges
+    A.tiles = tiles;
 #define GS_BLEND_LAUNCH(T_, S_, M_) \
     (void)launch_pdl(ctx->stream, blend_kernel<T_, S_, M_>, dim3(tiles), dim3(T_ * T_), 0, A)
 #define GS_BLEND_TILES(S_, M_)                                                             \

@@ -39,14 +39,15 @@ namespace {
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
-constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr uint32_t kNoDigit = 0xffffffffu;
 constexpr int kLookWindow = 16;  // predecessors inspected per look-back step
 
 // Keys present in the buffer: none when the emit was skipped (keys over
-// capacity, or batch cameras over the frame's tile/pixel capacity).
+// capacity, or batch cameras over the frame's tile/pixel capacity), and none
+// once a look-back wait has given up (the pass that gave up may have placed
+// keys wrongly, so no later pass, range or blend reads them).
 __device__ __forceinline__ uint32_t frame_keys(const uint32_t* status) {
-    return ((status[2] & GS_FLAG_CAPACITY) || status[3]) ? 0u : status[0];
+    return ((status[2] & (GS_FLAG_CAPACITY | GS_FLAG_TIMEOUT)) || status[3]) ? 0u : status[0];
 }
 
 struct HistArgs {
@@ -125,6 +126,8 @@ struct PassArgs {
     uint32_t* ticket;
     const uint32_t* method; // this pass's ranking method (set by sort_hist)
     int shift, dbits;
+    uint32_t spin_limit;    // polls per look-back wait before it gives up
+    int64_t withhold;       // partition that never publishes (wait-expiry test), else -1
 };
 
 struct PassSmem {
@@ -258,7 +261,8 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
     if (digit_thread) {
 #pragma unroll
         for (int w = 0; w < kSortThreads / 32; ++w) tot += S.wbase[w][t];
-        st_relaxed_gpu(A.lookback + (size_t)part * 256 + t, (part == 0 ? kFlagPrefix : kFlagAgg) | tot);
+        if ((int64_t)part != A.withhold)
+            st_relaxed_gpu(A.lookback + (size_t)part * 256 + t, (part == 0 ? kFlagPrefix : kFlagAgg) | tot);
         // clear this partition's row of the next pass's table (that table's last
         // user was the previous pass, which has completed)
         if (A.lookback_next) A.lookback_next[(size_t)part * 256 + t] = 0;
@@ -334,14 +338,15 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
                 }
                 j -= m;
                 if (!found && m < kLookWindow && j >= 0) {
-                    if (++spins > kSpinLimit) {
+                    if (++spins > A.spin_limit) {
                         atomicOr(A.status + 2, GS_FLAG_TIMEOUT);
                         break;
                     }
                     __nanosleep(32);
                 }
             }
-            st_relaxed_gpu(A.lookback + (size_t)part * 256 + t, kFlagPrefix | (prefix + tot));
+            if ((int64_t)part != A.withhold)
+                st_relaxed_gpu(A.lookback + (size_t)part * 256 + t, kFlagPrefix | (prefix + tot));
         }
         S.gbase[t] = dstart + prefix - boff;  // modular: gbase + staging index = output index
     }
@@ -425,6 +430,8 @@ gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override) {
         A.method = method + p;
         A.shift = p * dbits;
         A.dbits = dbits;
+        A.spin_limit = ctx->sort_spin_limit;
+        A.withhold = ctx->sort_withhold;
         (void)launch_pdl(ctx->stream, sort_pass_kernel, dim3((unsigned)parts), dim3(kSortThreads), sizeof(PassSmem), A);
         ctx->launches += 1;
     }

@@ -72,7 +72,7 @@ class GsFrameBytes(ctypes.Structure):
 EXPORTS = ["gs_create", "gs_destroy", "gs_set_stream", "gs_last_error", "gs_launch_count", "gs_frame_sizes",
            "gs_preprocess", "gs_intersect", "gs_sort", "gs_tile_ranges", "gs_render", "gs_render_stats",
            "gs_forward", "gs_read_status", "gs_backward_work_bytes", "gs_render_backward", "gs_intersect_noalloc",
-           "gs_batch_sizes", "gs_forward_batch", "gs_batch_status"]
+           "gs_batch_sizes", "gs_forward_batch", "gs_batch_status", "gs_read_culled", "gs_set_sort_wait"]
 
 _lib = None
 
@@ -111,6 +111,8 @@ def load(path=None) -> ctypes.CDLL:
     L.gs_batch_status.argtypes = [P, POINTER(GsBatchFrame), POINTER(c_int64), POINTER(c_uint32)]
     L.gs_intersect_noalloc.argtypes = [P, POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame),
                                        POINTER(c_int64)]
+    L.gs_read_culled.argtypes = [P, POINTER(GsFrame), POINTER(c_int64)]
+    L.gs_set_sort_wait.argtypes = [P, c_uint32, c_int64]
     L.gs_render_backward.argtypes = [P, POINTER(GsScene), POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame),
                                      P, POINTER(GsGrads)]
     for name in EXPORTS:
@@ -184,7 +186,7 @@ class Frame:
         self.image = torch.empty(3, height, width, dtype=torch.float32, device=device)
         self.final_T = torch.empty(height, width, dtype=torch.float32, device=device)
         self.last = torch.empty(height, width, dtype=torch.int32, device=device)
-        self.scratch = e(sz.scratch, torch.uint8, 1)
+        self.scratch = torch.zeros(max(sz.scratch, 1), dtype=torch.uint8, device=device)
         self.bytes = sz
         f = GsFrame()
         f.n_capacity, f.key_capacity = n, key_capacity
@@ -337,6 +339,14 @@ class Rasterizer:
         if st != 0 and (raise_on_error or st not in (1, 3, 5) or not fl.value):
             self._check(st, "gs_batch_status")  # CUDA errors always raise
         return int(k.value), int(fl.value)
+
+    def gs_read_culled(self, frame: Frame) -> int:
+        k = c_int64(0)
+        self._check(self.lib.gs_read_culled(self.ctx, ctypes.byref(frame.struct), ctypes.byref(k)), "gs_read_culled")
+        return int(k.value)
+
+    def gs_set_sort_wait(self, max_polls: int = 0, withhold_partition: int = -1):
+        self._check(self.lib.gs_set_sort_wait(self.ctx, int(max_polls), int(withhold_partition)), "gs_set_sort_wait")
 
     def gs_read_status(self, frame: Frame, raise_on_error: bool = True):
         k = c_int64(0)

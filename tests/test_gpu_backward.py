@@ -168,3 +168,98 @@ def test_differentiable_1m_980x545_l1_dssim(raster):
         assert e <= 1e-3, (k, e)
     assert rel_l2(diff.score.cpu().numpy().astype(np.float64), g2d[9]) <= 1e-3
     print(f"1M diff render: loss {float(loss.detach()):.5f}, score nonzero {int((g2d[9] > 0).sum())}")
+
+
+def window_fd(scene_np, cam, W, key, idx, box, h):
+    """Central difference of L = sum(W * image) over a pixel window of the
+    FP64 oracle's forward, by parameter `key`[idx] with step h.  The window
+    (x0, y0, x1, y1) holds every pixel the perturbed Gaussian reaches, so the
+    loss change over the whole image equals the change inside it; it is
+    rendered through a camera whose principal point is shifted by (x0, y0)."""
+    x0, y0, x1, y1 = box
+    wcam = synth.Camera(x1 - x0, y1 - y0, cam.fx, cam.fy, cam.cx - x0, cam.cy - y0, cam.tan_fovx, cam.tan_fovy,
+                        cam.viewmat, cam.campos, cam.near_z)
+    Wc = W[:, y0:y1, x0:x1]
+    arr = scene_np[key]
+    x = arr[idx]
+    vals = []
+    for s in (h, -h):
+        arr[idx] = np.float32(x + s)
+        vals.append(float(arr[idx]))
+        img = oracle.render(NpScene(scene_np), wcam, 16, 2, prec64=True, omp=True, key_cap=1 << 22)["image"]
+        vals.append(float((Wc * img).sum()))
+    arr[idx] = x
+    return (vals[1] - vals[3]) / (vals[0] - vals[2])
+
+
+class NpScene:
+    def __init__(self, d, deg=3):
+        for k, v in d.items():
+            setattr(self, k, v)
+        self.sh_degree = deg
+
+
+def fd_check(scene_np, cam, W, grads, state, rng, count=64, rel_step=1e-5):
+    """Check `count` random parameters of Gaussians that reach a pixel:
+    Richardson-extrapolated central differences (steps h, h/2) of the FP64
+    oracle forward against grads[key][idx].  A parameter whose two difference
+    quotients disagree (its perturbation crossed a threshold, clamp, stop or
+    depth-order decision) is skipped and redrawn; returns (errors, skipped)."""
+    n = scene_np["means"].shape[1]
+    u, v, a, b, c, t = (state[k] for k in ("u", "v", "a", "b", "c", "t"))
+    cand = np.nonzero(state["reach"])[0]
+    rms = {k: np.sqrt(np.mean(grads[k] ** 2)) for k in KEYS}
+    errs, skipped, trial = [], 0, 0
+    while len(errs) < count and trial < 4 * count:
+        key = KEYS[trial % 5]
+        trial += 1
+        i = int(rng.choice(cand))
+        idx = {"means": (int(rng.integers(3)), i), "scales": (int(rng.integers(3)), i),
+               "rotations": (int(rng.integers(4)), i), "opacities": (i,),
+               "sh": (int(rng.integers(16)), int(rng.integers(3)), i)}[key]
+        D = a[i] * c[i] - b[i] * b[i]
+        hx, hy = np.sqrt(t[i] * c[i] / D), np.sqrt(t[i] * a[i] / D)
+        box = (max(int(np.floor(u[i] - hx)) - 2, 0), max(int(np.floor(v[i] - hy)) - 2, 0),
+               min(int(np.ceil(u[i] + hx)) + 3, cam.width), min(int(np.ceil(v[i] + hy)) + 3, cam.height))
+        h = max(abs(float(scene_np[key][idx])) * rel_step, 1e-6)
+        f1 = window_fd(scene_np, cam, W, key, idx, box, h)
+        f2 = window_fd(scene_np, cam, W, key, idx, box, h / 2)
+        denom = max(abs(f2), 1e-3 * rms[key], 1e-30)
+        if abs(f1 - f2) > 1e-4 * denom:
+            skipped += 1
+            continue
+        fd = (4.0 * f2 - f1) / 3.0
+        errs.append((key, idx, float(grads[key][idx]), fd, abs(float(grads[key][idx]) - fd) / denom))
+    return errs, skipped
+
+
+def test_finite_differences_1m_980x545(raster):
+    """Config 3's check: 64 random parameters of the 1M-Gaussian scene at
+    980x545, GPU gradients of sum(W * image) with W = dL/dimage of the
+    L1 + D-SSIM loss, against central differences of the FP64 oracle's
+    forward (rel err <= 1e-3, denominator floored at 1e-3 rms(grad); skipped
+    draws reported and bounded)."""
+    from paper_2412_00578_gb300 import losses
+
+    scene = synth.blob_scene(1_000_000, seed=2)
+    cam = synth.pinhole(980, 545, 60.0, np.eye(3), np.array([0.0, 0.0, 25.0]))
+    gen = torch.Generator().manual_seed(3)
+    target_scene = synth.Scene(scene.means + 0.01 * torch.randn(scene.means.shape, generator=gen), scene.scales,
+                               scene.rotations, scene.opacities, scene.sh + 0.1 * torch.randn(scene.sh.shape, generator=gen))
+    r = raster.Renderer("cuda:0")
+    target = r.render(target_scene.to("cuda:0"), cam, "accutile", 16).image.clone()
+    img = r.render(scene.to("cuda:0"), cam, "accutile", 16).image.clone().requires_grad_(True)
+    losses.gs_loss(img, target).backward()
+    W = img.grad.detach().cpu().numpy().astype(np.float64)
+    g, out = gpu_grads(raster, scene, cam, W, 2)
+    P = out.frame.proj_planes().cpu().numpy()[:, : scene.n]
+    state = {"u": P[0, :, 0].astype(np.float64), "v": P[0, :, 1].astype(np.float64),
+             "a": P[1, :, 0].astype(np.float64), "b": P[1, :, 1].astype(np.float64),
+             "c": P[1, :, 2].astype(np.float64), "t": P[1, :, 3].astype(np.float64),
+             "reach": g["score"] > 0}
+    scene_np = {k: np.array(getattr(scene, k).numpy(), copy=True) for k in KEYS}
+    errs, skipped = fd_check(scene_np, cam, W, g, state, np.random.default_rng(4))
+    worst = max(errs, key=lambda e: e[4])
+    print(f"FD 1M 980x545: {len(errs)} parameters, {skipped} skipped, max rel err {worst[4]:.2e} ({worst[:2]})")
+    assert len(errs) == 64 and skipped <= 64
+    assert worst[4] <= 1e-3, worst

@@ -65,21 +65,64 @@ def test_graph_replay_with_new_poses(raster):
     ds = scene.to("cuda:0")
     gen = torch.Generator().manual_seed(73)
     cams2 = [synth.orbit_camera(gen, c.width, c.height) for c in cams]
-    br = raster.BatchRenderer("cuda:0", tile=16)
-    br.capture(ds, cams)
-    br.replay(cams2)
-    torch.cuda.synchronize()
-    got = [im.cpu().numpy().copy() for im in br.frame.images(cams2)]
-    K, flags = br.rast.gs_batch_status(br.frame, raise_on_error=False)
     direct = raster.BatchRenderer("cuda:0", tile=16)
-    ref, _ = direct.render(ds, cams2)
-    if flags == 0:  # the replay fit the captured key capacity
-        for a, b in zip(got, ref):
-            assert np.array_equal(a, b.cpu().numpy())
-    else:
-        assert flags & raster.FLAG_CAPACITY
-    br.replay()  # and again with the same poses
-    torch.cuda.synchronize()
+    ref, K2 = direct.render(ds, cams2)
+    ref = [im.cpu().numpy().copy() for im in ref]
+    br = raster.BatchRenderer("cuda:0", tile=16)
+    # capacities sized for both pose sets, so no replay can overflow
+    _, K1 = br.render(ds, cams)
+    br.ensure(scene.n, cams, min_keys=2 * max(K1, K2))
+    br.capture(ds, cams)
+    for poses, want in ((cams2, ref), (cams, None), (cams2, ref)):
+        br.replay(poses)
+        torch.cuda.synchronize()
+        K, flags = br.rast.gs_batch_status(br.frame, raise_on_error=False)
+        assert flags == 0
+        got = [im.cpu().numpy().copy() for im in br.frame.images(poses)]
+        if want is None:
+            want = [im.cpu().numpy().copy() for im in direct.render(ds, poses)[0]]
+            assert K == K1
+        else:
+            assert K == K2
+        for a, b in zip(got, want):
+            assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("mode,tile", [(2, 16), (0, 16), (1, 8), (2, 32)])
+def test_batch_against_oracle(raster, mode, tile):
+    """Every camera of a batch, one per resolution of the multi-view workload
+    (640x480, 980x545, 1332x876, 1920x1080), against the FP32 oracle: the
+    camera's sorted keys and tile ranges bit-exact, image within 1e-4."""
+    import oracle
+
+    scene = synth.blob_scene(20000, seed=76, n_blobs=20)
+    gen = torch.Generator().manual_seed(77)
+    cams = [synth.orbit_camera(gen, w, h) for (w, h) in synth.RESOLUTIONS]
+    ds = scene.to("cuda:0")
+    br = raster.BatchRenderer("cuda:0", tile=tile, mode=mode, bg=(0.1, 0.2, 0.3))
+    imgs, K = br.render(ds, cams)
+    imgs = [im.cpu().numpy().copy() for im in imgs]
+    keys = br.frame.keys[:K].cpu().numpy().view(np.uint64)
+    vals = br.frame.vals[:K].cpu().numpy().view(np.uint32)
+    ranges = br.frame.ranges.cpu().numpy().view(np.uint32)
+    toff, _, _, _ = raster.batch_layout(cams, tile)
+    tiles = (keys >> np.uint64(32)).astype(np.int64)
+    total = 0
+    for c, cam in enumerate(cams):
+        ref = oracle.render(scene, cam, tile, mode, bg=(0.1, 0.2, 0.3), prec64=False)
+        gx, gy = ref["grid"]
+        sel = (tiles >= toff[c]) & (tiles < toff[c] + gx * gy)
+        kb = (tiles[sel] - toff[c]).astype(np.uint64) << np.uint64(32) | (keys[sel] & np.uint64(0xffffffff))
+        assert np.array_equal(kb, ref["keys"]) and np.array_equal(vals[sel], ref["vals"]), c
+        # the camera's ranges, shifted back to the camera's own key list
+        r = ranges[2 * toff[c]: 2 * (toff[c] + gx * gy)].reshape(-1, 2).astype(np.int64)
+        first = int(np.nonzero(sel)[0][0]) if sel.any() else 0
+        r = np.where(r[:, 1:2] > r[:, 0:1], r - first, 0)
+        assert np.array_equal(r, ref["ranges"].astype(np.int64)), c
+        err = np.abs(imgs[c].astype(np.float64) - ref["image"]).max()
+        assert err <= 1e-4, (c, err)
+        total += ref["num_keys"]
+    assert total == K
 
 
 def test_batch_capacity_growth_and_overflow_flag(raster):

@@ -36,4 +36,20 @@ def test_served_results_equal_standalone_renders():
         img = ref.render(scenes[q.scene], q.camera, "accutile", 16).image
         assert torch.equal(q.result, img), q.rid
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
+    # a sample of served images, one per resolution and scene where present,
+    # against the FP32 oracle directly
+    import oracle
+
+    cpu = {k: synth.blob_scene(v.n, seed=80 if k == "s20k" else 81, n_blobs=20 if k == "s20k" else 30)
+           for k, v in scenes.items()}
+    seen = set()
+    for q in done:
+        key = (q.scene, q.camera.width, q.camera.height)
+        if key in seen:
+            continue
+        seen.add(key)
+        o = oracle.render(cpu[q.scene], q.camera, 16, 2, prec64=False)
+        err = np.abs(q.result.cpu().numpy().astype(np.float64) - o["image"]).max()
+        assert err <= 1e-4, (key, err)
+    assert len(seen) >= 4
     print(stats)
