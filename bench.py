@@ -799,7 +799,7 @@ def run_serving(args, dev, scene_3m):
 
     free, _ = torch.cuda.mem_get_info(dev)
     budget = int(0.5 * free)
-    ex = serve.GpuExecutor(scenes, dev, slots=3)
+    ex = serve.GpuExecutor(scenes, dev, slots=3, keep_results=False)
     warm = serve.poisson_requests(500.0, 0.05, list(scenes), cam_fn, seed=99)  # sizes the slot frames
     serve.serve(warm, serve.Scheduler({k: v.n for k, v in scenes.items()}, max_batch=16, memory_budget=budget), ex)
     out = {"scenes": {k: v.n for k, v in scenes.items()}, "slots": 3, "max_batch": 16,

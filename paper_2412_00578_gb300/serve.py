@@ -39,6 +39,8 @@ class Request:
     done: float | None = None      # when its result was observed complete
     result: object = None
     batch: int | None = None
+    deadline: float | None = None  # seconds after arrival by which it must have started
+    status: str = "pending"        # pending | done | expired | cancelled
 
     @property
     def latency(self) -> float:
@@ -67,6 +69,23 @@ class Scheduler:
 
     def submit(self, req: Request):
         self.waiting[req.rid] = req
+
+    def cancel(self, rid: int) -> bool:
+        """Withdraw a waiting request (False if it is not waiting: already in a
+        batch on the GPU, finished, or unknown)."""
+        r = self.waiting.pop(rid, None)
+        if r is None:
+            return False
+        r.status = "cancelled"
+        return True
+
+    def expire(self, now: float):
+        """Drop the waiting requests whose deadline has passed at time ``now``."""
+        gone = [r for r in self.waiting.values() if r.deadline is not None and now > r.arrival + r.deadline]
+        for r in gone:
+            del self.waiting[r.rid]
+            r.status = "expired"
+        return gone
 
     def next_batch(self):
         """Requests for one batch (same scene), or [] if nothing is admissible."""
@@ -100,7 +119,8 @@ class Scheduler:
 class GpuExecutor:
     """``slots`` concurrent batch renderers, each on its own CUDA stream."""
 
-    def __init__(self, scenes: dict, device=None, slots: int = 3, tile: int = 16, mode: str = "accutile"):
+    def __init__(self, scenes: dict, device=None, slots: int = 3, tile: int = 16, mode: str = "accutile",
+                 keep_results: bool = True):
         import torch
 
         from . import raster
@@ -116,6 +136,9 @@ class GpuExecutor:
             self.renderers.append(r)
         self.busy = [None] * slots  # (requests, nbytes, event, batch id) per slot
         self.raster = raster
+        # keep_results: clone each finished image for the caller (device
+        # memory per request); otherwise only its completion is recorded
+        self.keep_results = keep_results
 
     def free_slots(self):
         return [k for k, b in enumerate(self.busy) if b is None]
@@ -156,22 +179,27 @@ class GpuExecutor:
                 continue
             if flags:
                 r.rast.gs_batch_status(r.frame, raise_on_error=True)
-            with torch.cuda.stream(self.streams[k]):
-                imgs = r.frame.images(cams)
-                for q, im in zip(reqs, imgs):
-                    q.result = im.clone()
-            self.streams[k].synchronize()
+            if self.keep_results:
+                with torch.cuda.stream(self.streams[k]):
+                    imgs = r.frame.images(cams)
+                    for q, im in zip(reqs, imgs):
+                        q.result = im.clone()
+                self.streams[k].synchronize()
             self.busy[k] = None
             out.append((k, reqs, nbytes, bid))
         return out
 
 
-def serve(requests, scheduler: Scheduler, executor, clock=time.perf_counter, idle_sleep=5e-5):
+def serve(requests, scheduler: Scheduler, executor, clock=time.perf_counter, idle_sleep=5e-5, cancels=()):
     """Run the request stream to completion in real time.  ``requests`` are
-    sorted by arrival (seconds after start).  Returns the finished requests
-    and a stats dict."""
+    sorted by arrival (seconds after start).  A request with a ``deadline``
+    that has not started within it is dropped (expired); ``cancels`` lists
+    (time, rid) withdrawals, honoured while the request still waits.  Returns
+    the finished requests and a stats dict."""
     pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+    cancel_q = collections.deque(sorted(cancels))
     finished = []
+    expired, cancelled = [], []
     t0 = clock()
     batch_id = 0
     max_inflight = 0
@@ -180,10 +208,16 @@ def serve(requests, scheduler: Scheduler, executor, clock=time.perf_counter, idl
         now = clock() - t0
         while pending and pending[0].arrival <= now:
             scheduler.submit(pending.popleft())
+        while cancel_q and cancel_q[0][0] <= now:
+            rid = cancel_q.popleft()[1]
+            if scheduler.cancel(rid):
+                cancelled.append(rid)
+        expired.extend(scheduler.expire(now))
         for k, reqs, nbytes, _ in executor.poll():
             t = clock() - t0
             for q in reqs:
                 q.done = t
+                q.status = "done"
             finished.extend(reqs)
             scheduler.release(nbytes)
         for slot in executor.free_slots():
@@ -211,6 +245,8 @@ def serve(requests, scheduler: Scheduler, executor, clock=time.perf_counter, idl
         "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
         "frames_per_s": len(finished) / span if span > 0 else None,
         "span_s": span,
+        "expired": len(expired),
+        "cancelled": len(cancelled),
     }
     return finished, stats
 

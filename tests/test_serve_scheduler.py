@@ -92,3 +92,29 @@ def test_oldest_scene_goes_first():
     assert [r.rid for r in reqs] == [0, 2, 4]
     reqs, _ = sch.next_batch()
     assert [r.rid for r in reqs] == [1, 3]
+
+
+def test_expiry_and_cancellation():
+    """A request that waits past its deadline is dropped, never launched; a
+    cancel withdraws a request that is still waiting and is ignored once the
+    request is on the GPU; everything else completes."""
+    clock = FakeClock()
+    sch = serve.Scheduler({"small": 1000, "big": 5000}, max_batch=2)
+    ex = FakeExecutor(clock, slots=1, batch_time=2e-2)  # slow: a queue builds up
+    reqs = make_requests(n=120, rate=4000.0)
+    for r in reqs:
+        r.deadline = 0.05
+    cancels = [(reqs[5].arrival + 1e-4, 5), (reqs[0].arrival + 0.5, 0)]
+    done, stats = serve.serve(reqs, sch, ex, clock=clock, idle_sleep=0, cancels=cancels)
+    launched = {i for _, ids, _, _ in ex.launched for i in ids}
+    by_status = {}
+    for r in reqs:
+        by_status.setdefault(r.status, []).append(r)
+    assert stats["expired"] == len(by_status.get("expired", [])) > 0
+    assert stats["cancelled"] == 1 and reqs[5].status == "cancelled" and 5 not in launched
+    assert reqs[0].status == "done"  # its cancel came after it had started
+    for r in by_status["expired"]:
+        assert r.rid not in launched and r.start is None
+    for r in done:
+        assert r.status == "done" and r.start - r.arrival <= r.deadline + 1e-3
+    assert len(done) + stats["expired"] + stats["cancelled"] == len(reqs)
