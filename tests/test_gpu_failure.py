@@ -100,7 +100,7 @@ def test_non_finite_parameters_culled_and_counted(raster, mode):
     m = raster.MODES[mode]
     ref = oracle.render(scene, cam, 16, m, bg=BG, prec64=False)
     rast = raster.Rasterizer("cuda:0")
-    frame = raster.Frame(scene.n, cam.width, cam.height, 16, ref["num_keys"] + 10, "cuda:0")
+    frame = raster.Frame(scene.n, cam.width, cam.height, 16, 2 * ref["num_keys"] + 10, "cuda:0")
     cfg = raster.cfg_struct(16, mode, BG)
     forward(raster, rast, scene.to("cuda:0"), cam, cfg, frame)
     K, flags = rast.gs_read_status(frame)
