@@ -62,6 +62,18 @@ gs_status check_cam(gs_context* ctx, const gs_camera* cam, const gs_frame* f) {
     return GS_OK;
 }
 
+gs_status check_scene(gs_context* ctx, const gs_scene* scene, const gs_frame* frame) {
+    if (!scene) return set_error(ctx, GS_ERR_INVALID, "scene is NULL");
+    if (scene->n < 0 || scene->n > frame->n_capacity)
+        return set_error(ctx, GS_ERR_INVALID, "scene n %lld exceeds frame n_capacity %lld", (long long)scene->n,
+                         (long long)frame->n_capacity);
+    if (scene->sh_degree < 0 || scene->sh_degree > 3)
+        return set_error(ctx, GS_ERR_INVALID, "sh_degree %d not in 0..3", scene->sh_degree);
+    if (scene->n > 0 && (!scene->means || !scene->scales || !scene->rotations || !scene->opacities || !scene->sh))
+        return set_error(ctx, GS_ERR_INVALID, "scene has a NULL array");
+    return GS_OK;
+}
+
 gs_status check_cfg(gs_context* ctx, const gs_raster_cfg* cfg, const gs_frame* f) {
     if (!cfg) return set_error(ctx, GS_ERR_INVALID, "cfg is NULL");
     if (cfg->tile != f->tile) return set_error(ctx, GS_ERR_INVALID, "cfg tile %d != frame tile %d", cfg->tile, f->tile);
@@ -196,14 +208,7 @@ gs_status gs_preprocess(gs_context* ctx, const gs_scene* scene, const gs_camera*
     FrameView v;
     if (!make_view(ctx, frame, &v)) return GS_ERR_INVALID;
     if ((st = check_cam(ctx, cam, frame)) || (st = check_cfg(ctx, cfg, frame))) return st;
-    if (!scene) return set_error(ctx, GS_ERR_INVALID, "scene is NULL");
-    if (scene->n < 0 || scene->n > frame->n_capacity)
-        return set_error(ctx, GS_ERR_INVALID, "scene n %lld exceeds frame n_capacity %lld", (long long)scene->n,
-                         (long long)frame->n_capacity);
-    if (scene->sh_degree < 0 || scene->sh_degree > 3)
-        return set_error(ctx, GS_ERR_INVALID, "sh_degree %d not in 0..3", scene->sh_degree);
-    if (scene->n > 0 && (!scene->means || !scene->scales || !scene->rotations || !scene->opacities || !scene->sh))
-        return set_error(ctx, GS_ERR_INVALID, "scene has a NULL array");
+    if ((st = check_scene(ctx, scene, frame))) return st;
     return launch_preprocess(ctx, scene, cam, cfg, v);
 }
 
@@ -272,12 +277,17 @@ gs_status gs_render_stats(gs_context* ctx, const gs_camera* cam, const gs_raster
 
 gs_status gs_forward(gs_context* ctx, const gs_scene* scene, const gs_camera* cam, const gs_raster_cfg* cfg,
                      const gs_frame* frame) {
-    gs_status st;
-    if ((st = gs_preprocess(ctx, scene, cam, cfg, frame))) return st;
-    if ((st = gs_intersect(ctx, cam, cfg, frame, nullptr))) return st;
-    if ((st = gs_sort(ctx, cam, cfg, frame))) return st;
-    if ((st = gs_tile_ranges(ctx, cam, cfg, frame))) return st;
-    return gs_render(ctx, cam, cfg, frame);
+    gs_status st = enter(ctx);
+    if (st) return st;
+    FrameView v;
+    if (!make_view(ctx, frame, &v)) return GS_ERR_INVALID;
+    if ((st = check_cam(ctx, cam, frame)) || (st = check_cfg(ctx, cfg, frame))) return st;
+    if ((st = check_scene(ctx, scene, frame))) return st;
+    if ((st = launch_preprocess(ctx, scene, cam, cfg, v))) return st;
+    if ((st = launch_intersect(ctx, cfg, v))) return st;
+    if ((st = launch_sort(ctx, v, cfg->sort_digit_bits))) return st;
+    if ((st = launch_ranges(ctx, v))) return st;
+    return launch_render(ctx, cfg, v);
 }
 
 int64_t gs_backward_work_bytes(int64_t n_capacity) {

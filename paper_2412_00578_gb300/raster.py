@@ -369,9 +369,10 @@ class RenderOutput:
 class Renderer:
     """Forward renderer that owns frames and grows the key capacity on demand.
 
-    ``render`` runs the five stages asynchronously, then reads the frame
-    status (one synchronisation); if the keys did not fit it grows the
-    capacity to ``headroom`` x K and re-runs intersect, sort, ranges and render.
+    ``render`` runs gs_forward (the five stages, with preprocess, scan and
+    key emission fused) asynchronously, then reads the frame status (one
+    synchronisation); if the keys did not fit it grows the capacity to
+    ``headroom`` x K and renders the frame again.
     """
 
     def __init__(self, device=None, stream=None, headroom: float = 1.25):
@@ -394,22 +395,14 @@ class Renderer:
         f = self.frame(n, cam.width, cam.height, tile)
         r = self.rast
         f.generation += 1
-        r.gs_preprocess(scene, cam, cfg, f)
-        r.gs_intersect(cam, cfg, f)
-        r.gs_sort(cam, cfg, f)
-        r.gs_tile_ranges(cam, cfg, f)
-        r.gs_render(cam, cfg, f)
+        r.gs_forward(scene, cam, cfg, f)
         K, flags = r.gs_read_status(f, raise_on_error=False)
         if flags & FLAG_CAPACITY:
             if K > MAX_KEYS:
                 raise GsError(3, f"{K} keys exceed the library maximum {MAX_KEYS}")
             f = self.frame(n, cam.width, cam.height, tile, min_keys=int(K * self.headroom) + 1)
             f.generation += 1
-            r.gs_preprocess(scene, cam, cfg, f)
-            r.gs_intersect(cam, cfg, f)
-            r.gs_sort(cam, cfg, f)
-            r.gs_tile_ranges(cam, cfg, f)
-            r.gs_render(cam, cfg, f)
+            r.gs_forward(scene, cam, cfg, f)
             K, flags = r.gs_read_status(f, raise_on_error=False)
         if flags:
             r.gs_read_status(f, raise_on_error=True)

@@ -371,3 +371,77 @@ def test_outdoor_pruned_300k(raster, outdoor):
     assert out.num_keys == ref["num_keys"]
     assert np.array_equal(out.frame.keys[:out.num_keys].cpu().numpy().view(np.uint64), ref["keys"])
     assert np.abs(out.image.cpu().numpy().astype(np.float64) - ref["image"]).max() <= IMG_TOL
+
+
+# ---------------------------------------------------------------- gs_forward
+def run_forward(raster, rast, scene, cam, mode, tile, bg=(0.0, 0.0, 0.0), key_capacity=None, n_capacity=None):
+    """gs_forward: the five stages in one call, launched as one chain."""
+    ncap = scene.n if n_capacity is None else n_capacity
+    if key_capacity is None:
+        key_capacity = max(oracle.count_keys(scene, cam, tile, mode, prec64=False), 1)
+    frame = raster.Frame(ncap, cam.width, cam.height, tile, key_capacity, "cuda:0")
+    cfg = raster.cfg_struct(tile, mode, bg)
+    rast.gs_forward(scene.to("cuda:0"), cam, cfg, frame)
+    K, flags = rast.gs_read_status(frame, raise_on_error=False)
+    return frame, K, flags
+
+
+def check_forward(raster, rast, scene, cam, mode, tile, bg=(0.0, 0.0, 0.0), **kw):
+    frame, K, flags = run_forward(raster, rast, scene, cam, mode, tile, bg, **kw)
+    ref = oracle.render(scene, cam, tile, mode, bg=bg, prec64=False)
+    st, counts = oracle.preprocess(scene, cam, tile, mode, prec64=False)
+    assert flags == 0 and K == ref["num_keys"]
+    n = scene.n
+    assert np.array_equal(frame.counts[:n].cpu().numpy(), counts)
+    m = counts > 0
+    if m.any():
+        P = frame.proj_planes().cpu().numpy()[:, :n]
+        f32 = lambda a: a.astype(np.float32)
+        np.testing.assert_array_equal(P[0][m], f32(st[m][:, [0, 1, 3, 2]]))
+        np.testing.assert_array_equal(P[1][m], f32(st[m][:, [4, 5, 6, 7]]))
+        np.testing.assert_array_equal(P[2][m][:, :3], f32(st[m][:, [8, 9, 10]]))
+    assert np.array_equal(frame.keys[:K].cpu().numpy().view(np.uint64), ref["keys"])
+    assert np.array_equal(frame.vals[:K].cpu().numpy().view(np.uint32), ref["vals"])
+    assert np.array_equal(frame.tile_ranges().cpu().numpy().view(np.uint32), ref["ranges"])
+    assert np.abs(frame.image.cpu().numpy().astype(np.float64) - ref["image"]).max() <= IMG_TOL
+    assert np.array_equal(frame.last.cpu().numpy().view(np.uint32), ref["last"])
+    return frame, K
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_forward_ragged(raster, rast, mode, tile):
+    scene, cam = ragged_case()
+    check_forward(raster, rast, scene, cam, mode, tile, bg=(0.1, 0.2, 0.3))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_forward_many_blocks(raster, rast, mode):
+    """The 16k box (16 scan blocks, 9 sort partitions) and a capacity padded
+    past n (scan blocks with no Gaussians)."""
+    scene, cam = synth.small_box_workload()
+    check_forward(raster, rast, scene, cam, mode, 16)
+    check_forward(raster, rast, scene, cam, mode, 16, n_capacity=scene.n + 5000)
+
+
+def test_forward_large_splats_and_empty(raster, rast):
+    scene, cam = synth.small_box_workload(seed=3)
+    scene.scales = scene.scales * 8.0  # many multi-line AccuTile sets
+    for mode in (0, 1, 2):
+        check_forward(raster, rast, scene, cam, mode, 16)
+    empty = synth.uniform_box_scene(0, seed=1)
+    frame, K, flags = run_forward(raster, rast, empty, cam, 2, 16, bg=(0.2, 0.3, 0.4), key_capacity=16)
+    assert K == 0 and flags == 0
+    assert np.all(frame.image.cpu().numpy()[0] == np.float32(0.2))
+
+
+def test_forward_capacity_one_short(raster, rast):
+    scene, cam = synth.small_box_workload(seed=5)
+    K = oracle.count_keys(scene, cam, 16, 2)
+    frame, Kr, flags = run_forward(raster, rast, scene, cam, 2, 16, key_capacity=K - 1)
+    assert Kr == K and flags & raster.FLAG_CAPACITY
+    # nothing was sorted, ranged or blended: empty ranges, background
+    assert int(frame.tile_ranges().abs().sum()) == 0
+    assert float(frame.image.abs().max()) == 0.0
+    # the same frame buffers at capacity K render the oracle's frame
+    check_forward(raster, rast, scene, cam, 2, 16, key_capacity=K)
