@@ -28,7 +28,7 @@ _OUT = _HERE / "_build" / "liboracle.so"
 _OUT_OMP = _HERE / "_build" / "liboracle_omp.so"
 CXXFLAGS = ["-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
 
-MODES = {"3sigma": 0, "snugbox": 1, "accutile": 2}
+MODES = {"3sigma": 0, "snugbox": 1, "accutile": 2, "tbc": 3, "pixel": 4}
 
 
 def build(force: bool = False, omp: bool = False) -> Path:

@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <cstdint>
 #include <cstring>
 #include <numeric>
@@ -319,6 +320,9 @@ template <typename R> Proj<R> preprocess_one(const SceneIn& s, int64_t i, const 
 struct Grid {
     int T;       // tile edge in pixels
     int gx, gy;  // tiles per row / column
+    int W = 0, H = 0;  // image size in pixels (0: gx T by gy T)
+    int width() const { return W > 0 ? W : gx * T; }
+    int height() const { return H > 0 ? H : gy * T; }
 };
 
 
@@ -493,10 +497,93 @@ int64_t accutile_tiles(const Proj<R>& P, const Grid& g, int dir, Emit&& emit) {
     return cnt;
 }
 
+// q at offset (dx, dy) from the centre, in the blend's operation order
+// (render, Sec. 3.2.3): fma(dx, fma(a, dx, (2b) dy), (c dy) dy).
+template <typename R> R qpix(const Proj<R>& P, R dx, R dy) {
+    return std::fma(dx, std::fma(P.a, dx, (P.b + P.b) * dy), (P.c * dy) * dy);
+}
+
+// StopThePop tile-based culling (the paper's App. A.4 ablation; described
+// there, not printed).  Candidate tiles are those of an opacity-aware box
+// (Reading: the SnugBox rectangle); each candidate is kept iff the
+// Gaussian's alpha reaches 1/255 somewhere on the tile's closed square, i.e.
+// the minimum of q over [kx T, (kx+1) T] x [ky T, (ky+1) T] is <= t.  Reading
+// of the minimum: 0 if the centre lies in the square; otherwise the minimum
+// of this convex form lies on a face of the square facing the centre, and
+// along a face dx = X it is at dy = clamp(-b X / c) (symmetrically for a face
+// dy = Y); at most two faces face the centre.
+template <typename R> bool tile_reaches(const Proj<R>& P, R X0, R X1, R Y0, R Y1) {
+    const R dx0 = X0 - P.u, dx1 = X1 - P.u;
+    const R dy0 = Y0 - P.v, dy1 = Y1 - P.v;
+    const bool outx = dx0 > R(0) || dx1 < R(0);
+    const bool outy = dy0 > R(0) || dy1 < R(0);
+    if (!outx && !outy) return true;  // q = 0 <= t
+    R qmin = std::numeric_limits<R>::infinity();
+    if (outx) {
+        const R X = dx0 > R(0) ? dx0 : dx1;
+        const R d = std::min(std::max(((-P.b) * X) / P.c, dy0), dy1);
+        qmin = std::min(qmin, qpix(P, X, d));
+    }
+    if (outy) {
+        const R Y = dy0 > R(0) ? dy0 : dy1;
+        const R d = std::min(std::max(((-P.b) * Y) / P.a, dx0), dx1);
+        qmin = std::min(qmin, qpix(P, d, Y));
+    }
+    return qmin <= P.t;
+}
+
+template <typename R, typename Emit> int64_t tbc_tiles(const Proj<R>& P, const Grid& g, Emit&& emit) {
+    Snug<R> S = snugbox(P, g);
+    if (!S.ok) return 0;
+    const R T = R(g.T);
+    int64_t cnt = 0;
+    for (int ty = S.ty0; ty <= S.ty1; ++ty)
+        for (int tx = S.tx0; tx <= S.tx1; ++tx)
+            if (tile_reaches(P, R(tx) * T, R(tx + 1) * T, R(ty) * T, R(ty + 1) * T)) {
+                emit(tx, ty);
+                ++cnt;
+            }
+    return cnt;
+}
+
+// Pixel-exact tiles (the tile-set contract "tiles holding a pixel with
+// alpha >= 1/255" made literal): tile (tx, ty) is kept iff one of its pixels
+// inside the image has q <= t, with q evaluated exactly as the blend
+// evaluates it.  Written as its definition: every pixel of the SnugBox,
+// widened by one pixel on each side (so that rounding in the box can never
+// hide a pixel the blend would take), is tested.
+template <typename R, typename Emit> int64_t pixel_tiles(const Proj<R>& P, const Grid& g, Emit&& emit) {
+    Snug<R> S = snugbox(P, g);
+    if (!S.ok) return 0;
+    const int W = g.width(), H = g.height();
+    // floor(edge) -+ 1, clamped to the image (in double, so any float fits)
+    auto lo_px = [](double e, int n) { const double f = std::floor(e) - 1.0; return f < 0.0 ? 0 : (f > n ? n : int(f)); };
+    auto hi_px = [](double e, int n) { const double f = std::floor(e) + 1.0; return f < 0.0 ? -1 : (f > n - 1 ? n - 1 : int(f)); };
+    const int x0 = lo_px(double(S.x0), W), x1 = hi_px(double(S.x1), W);
+    const int y0 = lo_px(double(S.y0), H), y1 = hi_px(double(S.y1), H);
+    if (x0 > x1 || y0 > y1) return 0;
+    const int tx0 = x0 / g.T, tx1 = x1 / g.T, ty0 = y0 / g.T, ty1 = y1 / g.T;
+    std::vector<uint8_t> hit(size_t(tx1 - tx0 + 1) * size_t(ty1 - ty0 + 1), 0);
+    for (int py = y0; py <= y1; ++py)
+        for (int px = x0; px <= x1; ++px)
+            if (qpix(P, R(px) - P.u, R(py) - P.v) <= P.t)
+                hit[size_t(py / g.T - ty0) * size_t(tx1 - tx0 + 1) + size_t(px / g.T - tx0)] = 1;
+    int64_t cnt = 0;
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0; tx <= tx1; ++tx)
+            if (hit[size_t(ty - ty0) * size_t(tx1 - tx0 + 1) + size_t(tx - tx0)]) {
+                emit(tx, ty);
+                ++cnt;
+            }
+    return cnt;
+}
+
 template <typename R, typename Emit>
 int64_t mode_tiles(int mode, const Proj<R>& P, const Grid& g, Emit&& emit) {
     if (mode == 0) return sigma3_tiles(P, g, emit);
     if (mode == 1) return snugbox_tiles(P, g, emit);
+    if (mode == 3) return tbc_tiles(P, g, emit);
+    if (mode == 4) return pixel_tiles(P, g, emit);
     return accutile_tiles(P, g, 0, emit);
 }
 
@@ -579,6 +666,8 @@ Grid make_grid(int width, int height, int T) {
     g.T = T;
     g.gx = (width + T - 1) / T;
     g.gy = (height + T - 1) / T;
+    g.W = width;
+    g.H = height;
     return g;
 }
 

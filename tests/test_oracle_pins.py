@@ -530,3 +530,114 @@ def test_sigma3_golden_catches_planted_mistakes(mutant, tmp_path):
         return out[:k].copy()
 
     assert sigma3_failures(tiles), f"planted mistake {mutant} passed every golden case"
+
+
+# ---------------------------------------------------------------- tile-based culling and pixel-exact tiles
+TBC, PIX = 3, 4
+
+
+def random_ellipses(rng, count, T, gx, gy):
+    """Ellipses with random orientation, axis lengths from sub-pixel to a few
+    tiles, centres over and around a gx x gy grid of T-pixel tiles."""
+    out = []
+    for _ in range(count):
+        th = rng.uniform(0, np.pi)
+        s1, s2 = np.exp(rng.uniform(np.log(0.4), np.log(2.5 * T), 2))
+        Rm = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+        cov = Rm @ np.diag([s1 * s1, s2 * s2]) @ Rm.T + 0.3 * np.eye(2)
+        con = np.linalg.inv(cov)
+        u = rng.uniform(-T, (gx + 1) * T)
+        v = rng.uniform(-T, (gy + 1) * T)
+        t = rng.uniform(0.05, 11.0)
+        out.append((u, v, con[0, 0], con[0, 1], con[1, 1], t))
+    return out
+
+
+def test_tbc_tile_test_against_numerical_minimum():
+    """The tile-based culling test (App. A.4): a tile is kept iff the minimum
+    of q over its closed square is <= t.  Checked against scipy's bounded
+    quasi-Newton minimiser of the same quadratic on each candidate tile (ties
+    within 1e-7 t excluded)."""
+    from scipy.optimize import minimize
+
+    rng = np.random.default_rng(91)
+    T, gx, gy = 16, 6, 5
+    checked = 0
+    for e in random_ellipses(rng, 150, T, gx, gy):
+        u, v, a, b, c, t = e
+        ok, sb = oracle.snugbox(e, T, gx, gy, True)
+        if not ok:
+            continue
+        got = tile_set(oracle.ellipse_tiles(e, TBC, T, gx, gy, True))
+        q = lambda p: a * (p[0] - u) ** 2 + 2 * b * (p[0] - u) * (p[1] - v) + c * (p[1] - v) ** 2
+        for ty in range(int(sb[6]), int(sb[7]) + 1):
+            for tx in range(int(sb[4]), int(sb[5]) + 1):
+                box = [(tx * T, (tx + 1) * T), (ty * T, (ty + 1) * T)]
+                x0 = np.clip([u, v], [box[0][0], box[1][0]], [box[0][1], box[1][1]])
+                res = minimize(q, x0, bounds=box, method="L-BFGS-B", options={"ftol": 1e-15, "gtol": 1e-12})
+                m = min(float(res.fun), q(x0))
+                if abs(m - t) <= 1e-7 * t:
+                    continue
+                assert ((tx, ty) in got) == (m <= t), (e, tx, ty, m)
+                checked += 1
+    assert checked > 300
+
+
+def test_tbc_and_accutile_are_the_same_exact_set():
+    """In FP64 the culled SnugBox (tile-based culling) and the AccuTile sweep
+    are two algorithms for one set, the tiles whose closed square meets the
+    ellipse: equal on random ellipses and on the App. A.1 fixtures."""
+    rng = np.random.default_rng(92)
+    for T, gx, gy in ((16, 6, 5), (8, 9, 7)):
+        for e in random_ellipses(rng, 400, T, gx, gy):
+            tbc = tile_set(oracle.ellipse_tiles(e, TBC, T, gx, gy, True))
+            acc = tile_set(oracle.ellipse_tiles(e, ACCU, T, gx, gy, True))
+            assert tbc == acc, e
+
+
+def test_pixel_tiles_against_whole_image_brute_force():
+    """Pixel-exact tiles: the tiles of the pixels inside the image whose q
+    (in the blend's operation order) is <= t, found here by testing every
+    pixel of the image (the oracle tests only the widened SnugBox), in FP64
+    and FP32; the set nests inside AccuTile's (FP64)."""
+    rng = np.random.default_rng(93)
+    T, gx, gy = 8, 7, 6
+    W, H = gx * T, gy * T
+    X, Y = np.meshgrid(np.arange(W), np.arange(H))
+    surplus = total = 0
+    for e in random_ellipses(rng, 300, T, gx, gy):
+        u, v, a, b, c, t = e
+        for prec64, dt in ((True, np.float64), (False, np.float32)):
+            uu, vv, aa, bb, cc, tt = (dt(x) for x in e)
+            dx = X.astype(dt) - uu
+            dy = Y.astype(dt) - vv
+            if prec64:
+                q = dx * (aa * dx + (bb + bb) * dy) + (cc * dy) * dy
+            else:  # the FP32 order: fma(dx, fma(a, dx, (2b) dy), (c dy) dy), one rounding per fma
+                inner = (aa.astype(np.float64) * dx + ((bb + bb) * dy).astype(np.float64)).astype(np.float32)
+                q = (dx.astype(np.float64) * inner + ((cc * dy) * dy).astype(np.float64)).astype(np.float32)
+            hit = q <= tt
+            want = {(int(x) // T, int(y) // T) for x, y in zip(X[hit], Y[hit])}
+            got = tile_set(oracle.ellipse_tiles(e, PIX, T, gx, gy, prec64))
+            assert got == want, (e, prec64)
+            if prec64:
+                acc = tile_set(oracle.ellipse_tiles(e, ACCU, T, gx, gy, True))
+                assert got <= acc, e
+                surplus += len(acc - got)
+                total += len(acc)
+    assert 0 < surplus < total
+
+
+def test_new_modes_render_the_definition_image():
+    """Tile-based culling and pixel-exact tiles lose no contributing pixel:
+    their tiled images equal the tile-free image bit for bit, in FP32 and
+    FP64, and their key counts nest: pixel <= AccuTile = TBC <= SnugBox."""
+    scene, cam = small_case(seed=17)
+    for prec64 in (False, True):
+        ref = oracle.render_notile(scene, cam, prec64=prec64)["image"]
+        for mode in (TBC, PIX):
+            img = oracle.render(scene, cam, 16, mode, prec64=prec64)["image"]
+            assert np.array_equal(img, ref), (mode, prec64)
+    k = {m: oracle.count_keys(scene, cam, 16, m, prec64=True) for m in (SNUG, ACCU, TBC, PIX)}
+    assert k[PIX] <= k[ACCU] == k[TBC] <= k[SNUG]
+    assert k[PIX] < k[ACCU]
