@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--width", type=int, default=1280)
     p.add_argument("--height", type=int, default=840)
     p.add_argument("--tile", type=int, default=16)
-    p.add_argument("--modes", default="accutile,snugbox,3sigma",
+    p.add_argument("--modes", default="accutile,snugbox,3sigma,tbc,pixel",
                    help="modes to time; the first is the headline (profiling runs pass one mode)")
     p.add_argument("--stage-steps", type=int, default=10, help="frames per mode for the per-stage breakdown (0: skip)")
     p.add_argument("--no-cpu-baseline", action="store_true")

@@ -46,7 +46,11 @@ typedef enum gs_status {
 typedef enum gs_mode {
     GS_MODE_3SIGMA = 0,   /* 3D-GS square of radius ceil(3 sqrt(lambda_max)), Eq. radius */
     GS_MODE_SNUGBOX = 1,  /* tight box of the opacity-aware ellipse, Sec. 4.1.1       */
-    GS_MODE_ACCUTILE = 2  /* exact tiles of that ellipse, Sec. 4.1.2, Algorithm 1     */
+    GS_MODE_ACCUTILE = 2, /* exact tiles of that ellipse, Sec. 4.1.2, Algorithm 1     */
+    GS_MODE_TBC = 3,      /* tile-based culling, the StopThePop ablation of App. A.4:
+                             SnugBox tiles kept iff min of q over the tile <= t      */
+    GS_MODE_PIXEL = 4     /* pixel-exact: tiles holding an image pixel with q <= t
+                             (the blend's own test), so tile set = pixel set        */
 } gs_mode;
 
 /* Device status word flags (gs_read_status). */

@@ -77,7 +77,7 @@ gs_status check_scene(gs_context* ctx, const gs_scene* scene, const gs_frame* fr
 gs_status check_cfg(gs_context* ctx, const gs_raster_cfg* cfg, const gs_frame* f) {
     if (!cfg) return set_error(ctx, GS_ERR_INVALID, "cfg is NULL");
     if (cfg->tile != f->tile) return set_error(ctx, GS_ERR_INVALID, "cfg tile %d != frame tile %d", cfg->tile, f->tile);
-    if (cfg->mode < GS_MODE_3SIGMA || cfg->mode > GS_MODE_ACCUTILE)
+    if (cfg->mode < GS_MODE_3SIGMA || cfg->mode > GS_MODE_PIXEL)
         return set_error(ctx, GS_ERR_INVALID, "mode %d is not a gs_mode", cfg->mode);
     if (cfg->sort_digit_bits != 0 && (cfg->sort_digit_bits < 4 || cfg->sort_digit_bits > 8))
         return set_error(ctx, GS_ERR_INVALID, "sort_digit_bits %d not in {0, 4..8}", cfg->sort_digit_bits);

@@ -170,7 +170,7 @@ gs_status gs_forward_batch(gs_context* ctx, const gs_scene* scene, const gs_came
     if (!frame || !cfg || !scene || !cams) return set_error(ctx, GS_ERR_INVALID, "NULL argument");
     if (num_cams < 1 || num_cams > frame->max_cams)
         return set_error(ctx, GS_ERR_INVALID, "num_cams %d not in 1..max_cams (%d)", num_cams, frame->max_cams);
-    if (cfg->tile != frame->tile || cfg->mode < GS_MODE_3SIGMA || cfg->mode > GS_MODE_ACCUTILE ||
+    if (cfg->tile != frame->tile || cfg->mode < GS_MODE_3SIGMA || cfg->mode > GS_MODE_PIXEL ||
         (cfg->sort_digit_bits != 0 && (cfg->sort_digit_bits < 4 || cfg->sort_digit_bits > 8)))
         return set_error(ctx, GS_ERR_INVALID, "bad cfg (tile %d, mode %d, digit bits %d)", cfg->tile, cfg->mode,
                          cfg->sort_digit_bits);

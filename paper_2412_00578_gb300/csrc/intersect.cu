@@ -172,6 +172,8 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
                 const CamRec& R = A.table[cam];
                 grid.gx = R.gx;
                 grid.gy = R.gy;
+                grid.W = R.width;
+                grid.H = R.height;
                 tile0 = (uint32_t)R.tile_offset;
                 id = (uint32_t)(i - cam * A.cam_stride);
             }
@@ -185,9 +187,14 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
                 const Ellipse E{q0.x, q0.y, q1.x, q1.y, q1.z, q1.w};
                 Snug S;
                 if (snugbox(E, grid, S)) {
+                    auto put = [&](int tx, int ty) { W.put((uint32_t)(ty * grid.gx + tx)); };
                     if (A.mode == GS_MODE_SNUGBOX) {
                         for (int ty = S.R.y0; ty <= S.R.y1; ++ty)
                             for (int tx = S.R.x0; tx <= S.R.x1; ++tx) W.put((uint32_t)(ty * grid.gx + tx));
+                    } else if (A.mode == GS_MODE_TBC) {
+                        tbc_tiles(E, S, grid, put);
+                    } else if (A.mode == GS_MODE_PIXEL) {
+                        pixel_tiles(E, S, grid, put);
                     } else {
                         accutile_sweep(E, S, grid, W);
                     }
@@ -224,7 +231,7 @@ gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const Fram
         A.vals = v.vals0;
         A.n = v.ncap;
         A.mode = cfg->mode;
-        A.grid = Grid{(float)v.tile, v.gx, v.gy};
+        A.grid = Grid{(float)v.tile, v.gx, v.gy, v.width, v.height};
         A.table = v.table;
         A.cam_stride = v.cam_stride;
         if (v.table) (void)launch_pdl(ctx->stream, emit_kernel<true>, dim3((unsigned)nb), dim3(kScanThreads), 0, A);

@@ -79,7 +79,7 @@ extern "C" gs_status gs_intersect_noalloc(gs_context* ctx, const gs_camera* cam,
     if (st) return st;
     if (cam->width != frame->width || cam->height != frame->height)
         return set_error(ctx, GS_ERR_INVALID, "intersect_noalloc: camera does not match frame");
-    if (cfg->tile != frame->tile || cfg->mode < GS_MODE_3SIGMA || cfg->mode > GS_MODE_ACCUTILE)
+    if (cfg->tile != frame->tile || cfg->mode < GS_MODE_3SIGMA || cfg->mode > GS_MODE_PIXEL)
         return set_error(ctx, GS_ERR_INVALID, "intersect_noalloc: bad cfg (tile %d, mode %d)", cfg->tile, cfg->mode);
     gs_frame f = *frame;
     f.scratch = scratch;  // the caller's scratch pointer is neither needed nor touched

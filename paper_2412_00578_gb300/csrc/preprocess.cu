@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(256, 4) preprocess_multiview_kernel(const PreA
     const int64_t i = (int64_t)(blockIdx.x / (unsigned)A.num_cams) * blockDim.x + threadIdx.x;
     if (i >= A.ncap) return;
     const CamRec& R = A.table[cam];
-    const Grid g{A.grid.T, R.gx, R.gy};
+    const Grid g{A.grid.T, R.gx, R.gy, R.width, R.height};
     preprocess_one(A, R.k, g, i, (int64_t)cam * A.ncap + i);
 }
 
@@ -258,7 +258,7 @@ gs_status launch_preprocess(gs_context* ctx, const gs_scene* s, const gs_camera*
     A.ncap = v.ncap;
     A.sh_coeffs = (s->sh_degree + 1) * (s->sh_degree + 1);
     A.mode = cfg->mode;
-    A.grid = Grid{(float)v.tile, v.gx, v.gy};
+    A.grid = Grid{(float)v.tile, v.gx, v.gy, v.width, v.height};
     if (cam) {  // single camera: constants travel as kernel parameters
         A.cam.fx = cam->fx;
         A.cam.fy = cam->fy;

@@ -19,6 +19,7 @@ struct Ellipse {
 struct Grid {
     float T;      // tile edge, pixels (8, 16 or 32)
     int gx, gy;   // tiles per row, per column
+    int W = 0, H = 0;  // image size in pixels (the pixel-exact mode keeps pixels inside it)
     // 1/T.  T is a power of two, so x * invT is the exactly scaled x / T,
     // bit for bit the IEEE quotient, at the cost of one multiply.
     __host__ __device__ float invT() const { return T == 8.0f ? 0.125f : (T == 16.0f ? 0.0625f : 0.03125f); }
@@ -160,6 +161,95 @@ struct NoEmit {
     __device__ __forceinline__ void operator()(int, int, int, bool) const {}
 };
 
+// q at offset (dx, dy) from the centre, in the blend's operation order.
+__device__ __forceinline__ float qpix(const Ellipse& E, float dx, float dy) {
+    return fmaf(dx, fmaf(E.a, dx, (E.b + E.b) * dy), (E.c * dy) * dy);
+}
+
+// Tile-based culling (StopThePop, App. A.4): does q reach t on the closed
+// square [X0, X1] x [Y0, Y1]?  0 if the centre is inside; otherwise the
+// minimum lies on a face facing the centre, along face dx = X at
+// dy = clamp(-b X / c), along face dy = Y at dx = clamp(-b Y / a).
+__device__ __forceinline__ bool tile_reaches(const Ellipse& E, float X0, float X1, float Y0, float Y1) {
+    const float dx0 = X0 - E.u, dx1 = X1 - E.u;
+    const float dy0 = Y0 - E.v, dy1 = Y1 - E.v;
+    const bool outx = dx0 > 0.0f || dx1 < 0.0f;
+    const bool outy = dy0 > 0.0f || dy1 < 0.0f;
+    if (!outx && !outy) return true;
+    float qmin = INFINITY;
+    if (outx) {
+        const float X = dx0 > 0.0f ? dx0 : dx1;
+        const float d = fminf(fmaxf(((-E.b) * X) / E.c, dy0), dy1);
+        qmin = fminf(qmin, qpix(E, X, d));
+    }
+    if (outy) {
+        const float Y = dy0 > 0.0f ? dy0 : dy1;
+        const float d = fminf(fmaxf(((-E.b) * Y) / E.a, dx0), dx1);
+        qmin = fminf(qmin, qpix(E, d, Y));
+    }
+    return qmin <= E.t;
+}
+
+// Candidate tiles of the SnugBox rectangle kept by tile_reaches, row-major;
+// put(tx, ty) per kept tile; returns the count.
+template <class Put>
+__device__ __forceinline__ int tbc_tiles(const Ellipse& E, const Snug& S, const Grid& g, Put&& put) {
+    int cnt = 0;
+    for (int ty = S.R.y0; ty <= S.R.y1; ++ty)
+        for (int tx = S.R.x0; tx <= S.R.x1; ++tx)
+            if (tile_reaches(E, (float)tx * g.T, (float)(tx + 1) * g.T, (float)ty * g.T, (float)(ty + 1) * g.T)) {
+                put(tx, ty);
+                ++cnt;
+            }
+    return cnt;
+}
+
+// Pixel-exact tiles: tiles holding an image pixel with q <= t (the blend's
+// test).  The pixels tried are those of the SnugBox widened by one pixel on
+// each side, clipped to the image; within each tile the search stops at the
+// first pixel that passes.  Row-major; put(tx, ty) per kept tile.
+template <class Put>
+__device__ __forceinline__ int pixel_tiles(const Ellipse& E, const Snug& S, const Grid& g, Put&& put) {
+    auto lo_px = [](float e, int n) {
+        const float f = floorf(e) - 1.0f;
+        return f < 0.0f ? 0 : (f > (float)n ? n : (int)f);
+    };
+    auto hi_px = [](float e, int n) {
+        const float f = floorf(e) + 1.0f;
+        return f < 0.0f ? -1 : (f > (float)(n - 1) ? n - 1 : (int)f);
+    };
+    const int x0 = lo_px(S.x0, g.W), x1 = hi_px(S.x1, g.W);
+    const int y0 = lo_px(S.y0, g.H), y1 = hi_px(S.y1, g.H);
+    if (x0 > x1 || y0 > y1) return 0;
+    const int T = (int)g.T;
+    const int tx0 = x0 / T, tx1 = x1 / T, ty0 = y0 / T, ty1 = y1 / T;
+    int cnt = 0;
+    for (int ty = ty0; ty <= ty1; ++ty) {
+        const int py0 = max(y0, ty * T), py1 = min(y1, ty * T + T - 1);
+        for (int tx = tx0; tx <= tx1; ++tx) {
+            const int px0 = max(x0, tx * T), px1 = min(x1, tx * T + T - 1);
+            bool hit = false;
+            for (int py = py0; py <= py1 && !hit; ++py) {
+                const float dy = (float)py - E.v;
+                for (int px = px0; px <= px1; ++px)
+                    if (qpix(E, (float)px - E.u, dy) <= E.t) {
+                        hit = true;
+                        break;
+                    }
+            }
+            if (hit) {
+                put(tx, ty);
+                ++cnt;
+            }
+        }
+    }
+    return cnt;
+}
+
+struct NoPut {
+    __device__ __forceinline__ void operator()(int, int) const {}
+};
+
 // Tile count of one Gaussian in `mode` (0 when culled).
 __device__ __forceinline__ int tile_count(int mode, const Ellipse& E, int radius, const Grid& g) {
     if (mode == GS_MODE_3SIGMA) {
@@ -170,6 +260,8 @@ __device__ __forceinline__ int tile_count(int mode, const Ellipse& E, int radius
     Snug S;
     if (!snugbox(E, g, S)) return 0;
     if (mode == GS_MODE_SNUGBOX) return (S.R.x1 - S.R.x0 + 1) * (S.R.y1 - S.R.y0 + 1);
+    if (mode == GS_MODE_TBC) return tbc_tiles(E, S, g, NoPut{});
+    if (mode == GS_MODE_PIXEL) return pixel_tiles(E, S, g, NoPut{});
     return accutile_sweep(E, S, g, NoEmit{});
 }
 

@@ -15,7 +15,7 @@ import torch
 
 from . import build as _build
 
-MODES = {"3sigma": 0, "snugbox": 1, "accutile": 2}
+MODES = {"3sigma": 0, "snugbox": 1, "accutile": 2, "tbc": 3, "pixel": 4}
 MODE_NAMES = {v: k for k, v in MODES.items()}
 FLAG_CAPACITY = 1
 FLAG_TIMEOUT = 2

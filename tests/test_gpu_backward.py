@@ -49,7 +49,7 @@ def rel_l2(a, b):
     return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-30)
 
 
-@pytest.mark.parametrize("mode", [2, 1, 0])
+@pytest.mark.parametrize("mode", [2, 1, 0, 3, 4])
 @pytest.mark.parametrize("tile", [16, 8, 32])
 def test_gradients_match_oracle(raster, mode, tile):
     scene, cam = tiny_scene()

@@ -88,7 +88,7 @@ def test_graph_replay_with_new_poses(raster):
             assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("mode,tile", [(2, 16), (0, 16), (1, 8), (2, 32)])
+@pytest.mark.parametrize("mode,tile", [(2, 16), (0, 16), (1, 8), (2, 32), (3, 16), (4, 8), (4, 16)])
 def test_batch_against_oracle(raster, mode, tile):
     """Every camera of a batch, one per resolution of the multi-view workload
     (640x480, 980x545, 1332x876, 1920x1080), against the FP32 oracle: the

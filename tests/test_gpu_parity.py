@@ -112,7 +112,7 @@ def ragged_case(n=3000, seed=31, w=97, h=61):
     return scene, cam
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_ragged_small(raster, rast, mode, tile):
     scene, cam = ragged_case()
@@ -133,7 +133,7 @@ def test_render_stats_pair_counts(raster, rast, tile):
         assert co <= ex
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
 def test_box_16k_320x240(raster, rast, mode):
     scene, cam = synth.small_box_workload()
     gpu = run_pipeline(raster, rast, scene, cam, mode, 16)
@@ -145,7 +145,7 @@ def test_orbit_camera_large_splats(raster, rast):
     directions, clipping at every image edge)."""
     scene = synth.uniform_box_scene(4000, seed=32, half=3.0, log_scale_mu=-2.0, log_scale_sd=0.7)
     cam = synth.look_at(211, 157, 60.0, (2.5, -1.5, -6.0), (0.3, 0.2, 0.1))
-    for mode in (0, 1, 2):
+    for mode in (0, 1, 2, 3, 4):
         gpu = run_pipeline(raster, rast, scene, cam, mode, 16, bg=(0.5, 0.5, 0.5))
         check_against_oracle(gpu, scene, cam, mode, 16, bg=(0.5, 0.5, 0.5))
 
@@ -164,8 +164,9 @@ def test_needles_and_faint_splats(raster, rast, tile):
     faint = torch.rand(6000, generator=gen) < 0.3
     scene.opacities[faint] = 0.004 + 0.02 * torch.rand(int(faint.sum()), generator=gen)
     cam = synth.look_at(163, 119, 55.0, (0.7, -0.4, -5.5), (0.0, 0.0, 0.0))
-    gpu = run_pipeline(raster, rast, scene, cam, 2, tile, bg=(0.3, 0.1, 0.2))
-    check_against_oracle(gpu, scene, cam, 2, tile, bg=(0.3, 0.1, 0.2))
+    for mode in (2, 3, 4):
+        gpu = run_pipeline(raster, rast, scene, cam, mode, tile, bg=(0.3, 0.1, 0.2))
+        check_against_oracle(gpu, scene, cam, mode, tile, bg=(0.3, 0.1, 0.2))
 
 
 def crowded_tile_case(n, seed):
@@ -316,7 +317,7 @@ def outdoor():
     return synth.outdoor_workload()
 
 
-@pytest.mark.parametrize("mode", [2, 1, 0])
+@pytest.mark.parametrize("mode", [2, 1, 0, 3, 4])
 def test_outdoor_3m_1280x840_full_frame(raster, outdoor, mode):
     """The 3M-Gaussian 1280x840 workload in the launch configuration the
     benchmark times (gs_forward, tile 16): every key, range and pixel."""
@@ -329,7 +330,7 @@ def test_outdoor_3m_1280x840_full_frame(raster, outdoor, mode):
     f.keys.fill_(-1)
     r.rast.gs_forward(ds, cam, raster.cfg_struct(16, mode), f)  # the call the benchmark times
     K, flags = r.rast.gs_read_status(f)
-    ref = oracle.render(scene, cam, 16, mode, prec64=False)
+    ref = oracle.render(scene, cam, 16, mode, prec64=False, omp=True)
     assert K == ref["num_keys"] and flags == 0
     assert np.array_equal(f.keys[:K].cpu().numpy().view(np.uint64), ref["keys"])
     assert np.array_equal(f.vals[:K].cpu().numpy().view(np.uint32), ref["vals"])
@@ -408,14 +409,14 @@ def check_forward(raster, rast, scene, cam, mode, tile, bg=(0.0, 0.0, 0.0), **kw
     return frame, K
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_forward_ragged(raster, rast, mode, tile):
     scene, cam = ragged_case()
     check_forward(raster, rast, scene, cam, mode, tile, bg=(0.1, 0.2, 0.3))
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
 def test_forward_many_blocks(raster, rast, mode):
     """The 16k box (16 scan blocks, 9 sort partitions) and a capacity padded
     past n (scan blocks with no Gaussians)."""
