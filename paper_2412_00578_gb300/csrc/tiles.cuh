@@ -205,9 +205,16 @@ __device__ __forceinline__ int tbc_tiles(const Ellipse& E, const Snug& S, const 
 }
 
 // Pixel-exact tiles: tiles holding an image pixel with q <= t (the blend's
-// test).  The pixels tried are those of the SnugBox widened by one pixel on
-// each side, clipped to the image; within each tile the search stops at the
-// first pixel that passes.  Row-major; put(tx, ty) per kept tile.
+// test).  The pixels considered are those of the SnugBox widened by one pixel
+// on each side, clipped to the image.  Per pixel row the passing pixels form
+// one run around the row's chord centre xc = u - b dy / a (q restricted to a
+// row is a parabola with its minimum there): the run is seeded at the pixel
+// nearest xc (or its neighbour), and each end is found by testing pixels
+// from the chord's root estimate outwards or inwards, so every decision is
+// the blend's own q <= t.  A tile row whose pixel rows give tile spans that
+// do not overlap or touch (possible only for needles thinner than a pixel)
+// is settled by testing its tiles' pixels one by one.  Row-major;
+// put(tx, ty) per kept tile.
 template <class Put>
 __device__ __forceinline__ int pixel_tiles(const Ellipse& E, const Snug& S, const Grid& g, Put&& put) {
     auto lo_px = [](float e, int n) {
@@ -223,9 +230,51 @@ __device__ __forceinline__ int pixel_tiles(const Ellipse& E, const Snug& S, cons
     if (x0 > x1 || y0 > y1) return 0;
     const int T = (int)g.T;
     const int tx0 = x0 / T, tx1 = x1 / T, ty0 = y0 / T, ty1 = y1 / T;
+    auto clampi = [](float f, int lo, int hi) { return !(f >= (float)lo) ? lo : (f > (float)hi ? hi : (int)f); };
     int cnt = 0;
     for (int ty = ty0; ty <= ty1; ++ty) {
         const int py0 = max(y0, ty * T), py1 = min(y1, ty * T + T - 1);
+        int hl = 1 << 30, hh = -1;
+        bool gap = false;
+        for (int py = py0; py <= py1 && !gap; ++py) {
+            const float dy = (float)py - E.v;
+            auto pass = [&](int px) { return qpix(E, (float)px - E.u, dy) <= E.t; };
+            const float xc = E.u + ((-E.b) * dy) / E.a;
+            int s = clampi(floorf(xc + 0.5f), x0, x1);
+            if (!pass(s)) {
+                s = clampi((float)s + ((float)s <= xc ? 1.0f : -1.0f), x0, x1);
+                if (!pass(s)) continue;  // no pixel of this row reaches the ellipse
+            }
+            const float disc = (E.b * dy) * (E.b * dy) - E.a * ((E.c * dy) * dy - E.t);
+            const float half = disc > 0.0f ? sqrtf(disc) / E.a : 0.0f;
+            int L = clampi(ceilf(xc - half), x0, s);
+            if (pass(L)) {
+                while (L > x0 && pass(L - 1)) --L;
+            } else {
+                while (!pass(L)) ++L;  // ends at s at the latest
+            }
+            int R = clampi(floorf(xc + half), s, x1);
+            if (pass(R)) {
+                while (R < x1 && pass(R + 1)) ++R;
+            } else {
+                while (!pass(R)) --R;
+            }
+            const int a = L / T, b = R / T;
+            if (hh < 0) {
+                hl = a;
+                hh = b;
+            } else if (a > hh + 1 || b < hl - 1) {
+                gap = true;
+            } else {
+                hl = min(hl, a);
+                hh = max(hh, b);
+            }
+        }
+        if (!gap) {
+            for (int tx = hl; tx <= hh; ++tx) put(tx, ty);
+            cnt += hh >= 0 ? hh - hl + 1 : 0;
+            continue;
+        }
         for (int tx = tx0; tx <= tx1; ++tx) {
             const int px0 = max(x0, tx * T), px1 = min(x1, tx * T + T - 1);
             bool hit = false;
