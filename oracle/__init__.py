@@ -85,6 +85,7 @@ def _declare(L):
     L.oracle_blend_pixel.argtypes = [I32, P, I64, ctypes.c_double, ctypes.c_double, P, P]
     L.oracle_backward.argtypes = [I64, P, P, P, P, P, I32, I32, I32, P, I32, I32, P, P, P, P]
     L.oracle_sh_basis_grad.argtypes = [P, P, I64]
+    L.oracle_pup.argtypes = [I64, P, P, P, P, P, I32, I32, I32, P, I32, I32, P, P]
 
 
 def _ptr(a: np.ndarray):
@@ -260,6 +261,33 @@ def backward(scene, cam, dL_dimage, tile: int = 16, mode: int = 2, bg=(0.0, 0.0,
     out["sh"] = out["sh"].reshape(16, 3, n)
     out["opacities"] = out["opacities"].reshape(n)
     return out, g2d
+
+
+def pup(scene, cams, tile: int = 16, mode: int = 2, bg=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """PUP sensitivity H (FP64): [21, n], the upper triangle (row-major,
+    order mu_x mu_y mu_z s_0 s_1 s_2) of sum over the views ``cams``, pixels
+    and channels of grad_{mu,s} C grad_{mu,s} C^T through g_i (Sec. 4.2,
+    Eq. pup_score)."""
+    n, (m, s, r, o, sh), deg = _scene_arrays(scene)
+    bgv = np.asarray(bg, np.float32)
+    H = np.zeros((21, n), np.float64)
+    for cam in cams:
+        w, h, cf = _cam(cam)
+        lib().oracle_pup(n, _ptr(m), _ptr(s), _ptr(r), _ptr(o), _ptr(sh), deg, w, h, _ptr(cf), tile, mode, _ptr(bgv),
+                         _ptr(H))
+    return H
+
+
+def pup_full(H: np.ndarray) -> np.ndarray:
+    """[n, 6, 6] symmetric matrices from the [21, n] upper triangles."""
+    n = H.shape[1]
+    M = np.zeros((n, 6, 6))
+    e = 0
+    for a in range(6):
+        for b in range(a, 6):
+            M[:, a, b] = M[:, b, a] = H[e]
+            e += 1
+    return M
 
 
 def sh_basis_grad(dirs) -> np.ndarray:

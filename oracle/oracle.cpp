@@ -20,6 +20,7 @@
 // Readings of points where the paper is silent are marked "Reading:".
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <limits>
 #include <cstdint>
@@ -864,6 +865,128 @@ void blend_backward_pixel(const std::vector<Proj<double>>& P, const uint32_t* li
     }
 }
 
+// PUP sensitivity (Sec. 4.2, Eq. pup_score), FP64, one view added to
+// hess[21][n] (row-major upper triangle of the symmetric 6 x 6 block over
+// mu_x mu_y mu_z s_0 s_1 s_2).  Reading: the image's gradient with respect
+// to (mu_i, s_i) is taken through the 2D Gaussian value g_i(p), with the
+// colour's view dependence held fixed:
+//   grad C_ch(p) = dC_ch/dg_i * grad_{mu,s} g_i(p),
+// dC_ch/dg_i = sigma_i T_i (c_i,ch - B_ch) from the back-to-front walk of the
+// backward (zero where alpha is clamped at 0.99), and grad_{mu,s} g_i(p) =
+// J_i^T dg/d(u, v, a, b, c), where J_i, the Jacobian of (u, v, a, b, c) with
+// respect to (mu, s), is taken by central differences of this file's own
+// forward projection (steps h and h/2 on the float parameter, Richardson
+// extrapolated), not by the analytic chain.
+void pup_jacobian_fd(const SceneIn& s, int64_t i, const Cam<double>& cam, double J[5][6]) {
+    float mu[3] = {s.means[i], s.means[s.n + i], s.means[2 * s.n + i]};
+    float sc[3] = {s.scales[i], s.scales[s.n + i], s.scales[2 * s.n + i]};
+    float q[4] = {s.rots[i], s.rots[s.n + i], s.rots[2 * s.n + i], s.rots[3 * s.n + i]};
+    float op = s.opac[i];
+    float sh[48];
+    for (int k = 0; k < 48; ++k) sh[k] = 0.0f;
+    auto state = [&](double out[5]) {
+        float m3[3] = {mu[0], mu[1], mu[2]};
+        SceneIn one{1, 0, m3, sc, q, &op, sh};
+        Proj<double> P = preprocess_one<double>(one, 0, cam);
+        out[0] = P.u; out[1] = P.v; out[2] = P.a; out[3] = P.b; out[4] = P.c;
+    };
+    for (int j = 0; j < 6; ++j) {
+        float* x = j < 3 ? &mu[j] : &sc[j - 3];
+        const float x0 = *x;
+        const double h = std::max(std::fabs(double(x0)) * 1e-3, 1e-5);
+        double d[2][5];
+        for (int r = 0; r < 2; ++r) {
+            const double step = r == 0 ? h : h / 2;
+            double fp[5], fm[5];
+            *x = float(double(x0) + step);
+            const double xp = *x;
+            state(fp);
+            *x = float(double(x0) - step);
+            const double xm = *x;
+            state(fm);
+            *x = x0;
+            for (int k = 0; k < 5; ++k) d[r][k] = (fp[k] - fm[k]) / (xp - xm);
+        }
+        for (int k = 0; k < 5; ++k) J[k][j] = (4.0 * d[1][k] - d[0][k]) / 3.0;
+    }
+}
+
+void pup_view(const SceneIn& s, int width, int height, const float* camf, int tile, int mode, const float* bg,
+              double* hess) {
+    const int64_t n = s.n;
+    Cam<double> cam = make_cam<double>(width, height, camf);
+    Grid g = make_grid(width, height, tile);
+    std::vector<Proj<double>> P = preprocess_all<double>(s, cam);
+    std::vector<uint64_t> keys;
+    std::vector<uint32_t> vals;
+    for (int64_t i = 0; i < n; ++i) {
+        float depth_f = static_cast<float>(P[i].depth);
+        uint32_t dbits;
+        std::memcpy(&dbits, &depth_f, 4);
+        mode_tiles<double>(mode, P[i], g, [&](int tx, int ty) {
+            keys.push_back(((uint64_t(ty) * uint64_t(g.gx) + uint64_t(tx)) << 32) | uint64_t(dbits));
+            vals.push_back(static_cast<uint32_t>(i));
+        });
+    }
+    std::vector<int64_t> order(keys.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return keys[a] < keys[b]; });
+    std::vector<std::vector<uint32_t>> lists(size_t(g.gx) * size_t(g.gy));
+    for (int64_t k : order) lists[keys[k] >> 32].push_back(vals[k]);
+    std::vector<std::array<double, 30>> J(static_cast<size_t>(n));
+    std::vector<char> haveJ(size_t(n), 0);
+    for (int py = 0; py < height; ++py)
+        for (int px = 0; px < width; ++px) {
+            const auto& L = lists[size_t(py / tile) * size_t(g.gx) + size_t(px / tile)];
+            std::vector<Contrib<double>> cs;
+            double T = 1.0;
+            for (uint32_t id : L) {
+                const Proj<double>& G = P[id];
+                double dx = px - G.u, dy = py - G.v;
+                double q = std::fma(dx, std::fma(G.a, dx, (G.b + G.b) * dy), (G.c * dy) * dy);
+                if (!(q <= G.t)) continue;
+                double gg = std::exp(-0.5 * q);
+                double raw = G.opacity * gg;
+                double alpha = std::min(0.99, raw);
+                double Tn = T * (1.0 - alpha);
+                if (Tn < 1e-4) break;
+                cs.push_back({id, alpha, gg, T, q, dx, dy, raw > 0.99});
+                T = Tn;
+            }
+            double B[3] = {bg[0], bg[1], bg[2]};
+            for (size_t m = cs.size(); m-- > 0;) {
+                const Contrib<double>& e = cs[m];
+                const Proj<double>& G = P[e.idx];
+                if (!e.clamped) {
+                    double w = 0.0;
+                    for (int ch = 0; ch < 3; ++ch) {
+                        const double dCdg = G.opacity * e.T * (G.rgb[ch] - B[ch]);
+                        w += dCdg * dCdg;
+                    }
+                    if (!haveJ[e.idx]) {
+                        double Jm[5][6];
+                        pup_jacobian_fd(s, e.idx, cam, Jm);
+                        for (int k = 0; k < 30; ++k) J[e.idx][k] = Jm[k / 6][k % 6];
+                        haveJ[e.idx] = 1;
+                    }
+                    // dg/d(u, v, a, b, c) at this pixel
+                    const double hg = -0.5 * e.g;
+                    const double g5[5] = {hg * (-2.0 * (G.a * e.dx + G.b * e.dy)), hg * (-2.0 * (G.b * e.dx + G.c * e.dy)),
+                                          hg * e.dx * e.dx, hg * 2.0 * e.dx * e.dy, hg * e.dy * e.dy};
+                    double g6[6];
+                    for (int j = 0; j < 6; ++j) {
+                        g6[j] = 0.0;
+                        for (int k = 0; k < 5; ++k) g6[j] += J[e.idx][k * 6 + j] * g5[k];
+                    }
+                    int el = 0;
+                    for (int a = 0; a < 6; ++a)
+                        for (int b = a; b < 6; ++b) hess[int64_t(el++) * n + e.idx] += w * g6[a] * g6[b];
+                }
+                for (int ch = 0; ch < 3; ++ch) B[ch] = e.alpha * G.rgb[ch] + (1.0 - e.alpha) * B[ch];
+            }
+        }
+}
+
 // Derivatives of the SH basis (in the order of sh_basis) with respect to
 // the unit direction (x, y, z): dY[k][0..2].
 void sh_basis_grad(double x, double y, double z, double dY[16][3]) {
@@ -1249,6 +1372,14 @@ void oracle_backward(int64_t n, const float* means, const float* scales, const f
 }
 
 // SH basis gradient at unit directions dirs[n][3]; out[n][16][3].
+// PUP sensitivity of one view, added to hess[21][n] (FP64).
+void oracle_pup(int64_t n, const float* means, const float* scales, const float* rots, const float* opac,
+                const float* sh, int sh_degree, int width, int height, const float* camf, int tile, int mode,
+                const float* bg, double* hess) {
+    SceneIn s{n, sh_degree, means, scales, rots, opac, sh};
+    pup_view(s, width, height, camf, tile, mode, bg, hess);
+}
+
 void oracle_sh_basis_grad(const double* dirs, double* out, int64_t n) {
     for (int64_t i = 0; i < n; ++i) {
         double dY[16][3];

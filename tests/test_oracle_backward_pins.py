@@ -5,6 +5,7 @@ differences of the basis, and the pruning score against its closed form."""
 import math
 
 import numpy as np
+import torch
 import pytest
 
 import oracle
@@ -125,3 +126,72 @@ def test_pruning_score_single_gaussian_closed_form():
     inside = (q <= t) & (sig * np.exp(-q / 2) < 0.99)
     assert inside.sum() > 5
     assert g2d[9, 0] == pytest.approx(sig * sig * float((col ** 2).sum()) * inside.sum(), rel=1e-12)
+
+
+# ---------------------------------------------------------------- PUP sensitivity
+def pup_fd(d, cam, keys=("means", "scales"), rel=1e-3):
+    """grad_{mu,s} of every pixel and channel of the FP64 tile-free image, by
+    Richardson-extrapolated central differences, for every Gaussian:
+    returns [n, 6, 3 H W]."""
+    n = d["means"].shape[1]
+    out = np.zeros((n, 6, 3 * cam.height * cam.width))
+    for i in range(n):
+        j = 0
+        for key in keys:
+            for k in range(3):
+                x0 = d[key][k, i]
+                h = max(abs(float(x0)) * rel, 1e-5)
+                est = []
+                for step in (h, h / 2):
+                    dp = {kk: vv.copy() for kk, vv in d.items()}
+                    dm = {kk: vv.copy() for kk, vv in d.items()}
+                    dp[key][k, i] = np.float32(x0 + step)
+                    dm[key][k, i] = np.float32(x0 - step)
+                    he = float(dp[key][k, i]) - float(dm[key][k, i])
+                    ip = oracle.render_notile(NpScene(dp, 0), cam, prec64=True)["image"].ravel()
+                    im = oracle.render_notile(NpScene(dm, 0), cam, prec64=True)["image"].ravel()
+                    est.append((ip - im) / he)
+                out[i, j] = (4.0 * est[1] - est[0]) / 3.0
+                j += 1
+    return out
+
+
+def test_pup_sensitivity_against_finite_differences_of_the_image():
+    """PUP's H_i = sum_p sum_ch grad_{mu,s} C grad_{mu,s} C^T (Sec. 4.2, Eq.
+    pup_score), from the oracle's construction (back-to-front dC/dg, the
+    projection Jacobian by differences of the projection alone, analytic
+    dg/d(u, v, a, b, c)), against the same sum built from central
+    differences of the whole FP64 tile-free image, for three overlapping
+    Gaussians with view-independent colour (SH degree 0) whose ellipses have
+    no pixel near their threshold (so no inclusion decision moves)."""
+    cam = synth.look_at(40, 32, 60.0, (0.3, -0.2, -4.0), (0.0, 0.0, 0.0))
+    rng = np.random.default_rng(60)
+    for attempt in range(2000):
+        scene = synth.uniform_box_scene(3, seed=int(rng.integers(1 << 30)), half=0.25, log_scale_mu=-1.6,
+                                        log_scale_sd=0.3, sh_degree=0)
+        scene.opacities[:] = torch.tensor([0.6, 0.45, 0.8])
+        st, _ = oracle.preprocess(scene, cam, 16, 2, prec64=True)
+        X, Y = np.meshgrid(np.arange(cam.width), np.arange(cam.height))
+        margin = np.inf
+        for i in range(3):
+            u, v, a, b, c, t = st[i, [0, 1, 4, 5, 6, 7]]
+            dx, dy = X - u, Y - v
+            q = a * dx * dx + 2 * b * dx * dy + c * dy * dy
+            margin = min(margin, np.abs(q - t).min() / t)
+        if margin > 0.004 and st[:, 15].all():
+            break
+    else:
+        pytest.fail("no configuration without near-threshold pixels")
+    d = {k: np.array(getattr(scene, k).numpy(), copy=True) for k in ("means", "scales", "rotations", "opacities", "sh")}
+    D = pup_fd(d, cam, rel=1e-4)
+    H_fd = np.einsum("iap,ibp->iab", D, D)
+    H = oracle.pup_full(oracle.pup(NpScene(d, 0), [cam], 16, 2))
+    for i in range(3):
+        rel = np.linalg.norm(H[i] - H_fd[i]) / np.linalg.norm(H_fd[i])
+        assert rel <= 1e-6, (i, rel)
+    # one view gives a rank-deficient 6 x 6 block (the image sees only the 5
+    # parameters of the 2D Gaussian); a second view makes it definite
+    assert np.linalg.matrix_rank(H[0], tol=1e-9 * np.abs(H[0]).max()) <= 5
+    cam2 = synth.look_at(40, 32, 60.0, (-2.5, 1.0, -3.0), (0.0, 0.0, 0.0))
+    H2 = oracle.pup_full(oracle.pup(NpScene(d, 0), [cam, cam2], 16, 2))
+    assert np.all(np.linalg.eigvalsh(H2) > 0)
