@@ -248,6 +248,26 @@ int64_t gs_backward_work_bytes(int64_t n_capacity);
 gs_status gs_render_backward(gs_context* ctx, const gs_scene* scene, const gs_camera* cam, const gs_raster_cfg* cfg,
                              const gs_frame* frame, const float* dL_dimage, const gs_grads* grads);
 
+/* PUP sensitivity (the pruning score the paper builds on, Sec. 4.2, Eq.
+ * pup_score): U_i = log det H_i with
+ *   H_i = sum over views, pixels p and channels of
+ *         grad_{mu_i, s_i} C(p) grad_{mu_i, s_i} C(p)^T,
+ * the 6 x 6 block of the Gauss-Newton Hessian of the image with respect to
+ * the mean and the (activated) scale of Gaussian i, taken through its 2D
+ * value g_i(p) (the colour's view dependence is held fixed).  Memory: 21
+ * floats per Gaussian for H (the symmetric 6 x 6), against one for the
+ * efficient score of gs_render_backward.
+ * gs_pup_accumulate adds one view's terms to hessian ([21][n] device floats,
+ * row-major upper triangle in the order mu_x mu_y mu_z s_0 s_1 s_2) for the
+ * frame's completed forward render of this scene, camera and cfg; work is
+ * gs_pup_work_bytes(n_capacity) bytes of device scratch, 16-byte aligned.
+ * gs_pup_score writes U_i to score[n] (-inf where H_i is not positive
+ * definite, e.g. a Gaussian seen from a single view: rank <= 5). */
+int64_t gs_pup_work_bytes(int64_t n_capacity);
+gs_status gs_pup_accumulate(gs_context* ctx, const gs_scene* scene, const gs_camera* cam, const gs_raster_cfg* cfg,
+                            const gs_frame* frame, float* hessian, float* work);
+gs_status gs_pup_score(gs_context* ctx, const float* hessian, int64_t n, float* score);
+
 /* gs_intersect for callers that cannot allocate device memory (a plug-in
  * whose host application owns all GPU allocations, a real-time loop that must
  * not stall on an allocation, a program that forbids allocation after

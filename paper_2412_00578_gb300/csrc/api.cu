@@ -313,6 +313,28 @@ gs_status gs_render_backward(gs_context* ctx, const gs_scene* scene, const gs_ca
     return launch_backward(ctx, scene, cam, cfg, v, dL_dimage, grads);
 }
 
+int64_t gs_pup_work_bytes(int64_t n_capacity) { return n_capacity < 0 ? 0 : std::max<int64_t>(n_capacity * 64, 16); }
+
+gs_status gs_pup_accumulate(gs_context* ctx, const gs_scene* scene, const gs_camera* cam, const gs_raster_cfg* cfg,
+                            const gs_frame* frame, float* hessian, float* work) {
+    gs_status st = enter(ctx);
+    if (st) return st;
+    FrameView v;
+    if (!make_view(ctx, frame, &v)) return GS_ERR_INVALID;
+    if ((st = check_cam(ctx, cam, frame)) || (st = check_cfg(ctx, cfg, frame))) return st;
+    if ((st = check_scene(ctx, scene, frame))) return st;
+    if (!hessian || !work) return set_error(ctx, GS_ERR_INVALID, "pup: hessian and work are required");
+    if (reinterpret_cast<uintptr_t>(work) & 15) return set_error(ctx, GS_ERR_INVALID, "pup: work must be 16-byte aligned");
+    return launch_pup(ctx, scene, cam, cfg, v, hessian, work);
+}
+
+gs_status gs_pup_score(gs_context* ctx, const float* hessian, int64_t n, float* score) {
+    gs_status st = enter(ctx);
+    if (st) return st;
+    if (n < 0 || (n > 0 && (!hessian || !score))) return set_error(ctx, GS_ERR_INVALID, "pup_score: bad arguments");
+    return launch_pup_score(ctx, hessian, n, score);
+}
+
 gs_status gs_set_sort_wait(gs_context* ctx, uint32_t max_polls, int64_t withhold_partition) {
     if (!ctx) return GS_ERR_INVALID;
     ctx->sort_spin_limit = max_polls ? max_polls : kDefaultSpinLimit;

@@ -43,8 +43,15 @@ struct BwdArgs {
     float bg0, bg1, bg2;
 };
 
-template <int T>
+// kPup: instead of the gradients, accumulate the PUP sensitivity terms of
+// Sec. 4.2 (Eq. pup_score): per Gaussian, the 15 entries of the symmetric
+// 5x5 matrix sum_p w_p G5 G5^T, where G5 = dg/d(u, v, a, b, c) at the pixel
+// and w_p = sum_ch (dC_ch/dg)^2 (zero where alpha is clamped), into a
+// 16-float row.
+template <int T, bool kPup>
 __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_backward_kernel(const BwdArgs A) {
+    constexpr int kNV = kPup ? 15 : kWork;       // values per (pixel, Gaussian) pair
+    constexpr int kRow = kPup ? 16 : kWorkRow;   // floats per Gaussian row
     constexpr int NT = T * T;
     constexpr int NB = NT < 256 ? NT : 256;
     constexpr int NSX = T / kSubW;
@@ -71,9 +78,11 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_
     if (inside) {
         my_last = (int)A.last[o];
         Tr = A.final_T[o];
-        G0 = A.dL_dimg[o];
-        G1 = A.dL_dimg[HW + o];
-        G2 = A.dL_dimg[2 * HW + o];
+        if (!kPup) {
+            G0 = A.dL_dimg[o];
+            G1 = A.dL_dimg[HW + o];
+            G2 = A.dL_dimg[2 * HW + o];
+        }
     }
     float B0 = A.bg0, B1 = A.bg1, B2 = A.bg2;
     if (threadIdx.x == 0) s_maxlast = 0;
@@ -107,7 +116,7 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_
                 bits &= ~(1u << hb);
                 const int k = c0 + hb;
                 const int pos = b0 + k;  // 0-based position in the tile list
-                float v[kWork];
+                float v[16];
                 bool has = false;
                 if (pos < my_last) {
                     const float4 g0 = s_g0[k];
@@ -125,10 +134,27 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_
                         const float Tb = __fdividef(Tr, 1.0f - alpha);
                         const float4 col = s_g2[k];
                         const float w = alpha * Tb;
+                        const float d0 = Tb * (col.x - B0), d1 = Tb * (col.y - B1), d2 = Tb * (col.z - B2);
+                        if (kPup) {
+#pragma unroll
+                            for (int m = 0; m < 16; ++m) v[m] = 0.0f;
+                            if (raw <= 0.99f) {
+                                const float s0 = g1.z * d0, s1 = g1.z * d1, s2 = g1.z * d2;
+                                const float wp = s0 * s0 + s1 * s1 + s2 * s2;
+                                const float hg = -0.5f * g;
+                                const float a = g0.z, b = g1.w, c = g1.x;
+                                const float G5[5] = {hg * (-2.0f * (a * dx + b * dy)), hg * (-2.0f * (b * dx + c * dy)),
+                                                     hg * (dx * dx), hg * (2.0f * dx * dy), hg * (dy * dy)};
+                                int m = 0;
+#pragma unroll
+                                for (int r = 0; r < 5; ++r)
+#pragma unroll
+                                    for (int q2 = r; q2 < 5; ++q2) v[m++] = wp * G5[r] * G5[q2];
+                            }
+                        } else {
                         v[6] = G0 * w;
                         v[7] = G1 * w;
                         v[8] = G2 * w;
-                        const float d0 = Tb * (col.x - B0), d1 = Tb * (col.y - B1), d2 = Tb * (col.z - B2);
                         const float dL_dalpha = G0 * d0 + G1 * d1 + G2 * d2;
                         if (raw <= 0.99f) {
                             v[5] = dL_dalpha * g;
@@ -144,6 +170,7 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_
                         } else {
                             v[0] = v[1] = v[2] = v[3] = v[4] = v[5] = v[9] = 0.0f;
                         }
+                        }
                         B0 = alpha * col.x + (1.0f - alpha) * B0;
                         B1 = alpha * col.y + (1.0f - alpha) * B1;
                         B2 = alpha * col.z + (1.0f - alpha) * B2;
@@ -155,10 +182,15 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_
                     // up to sixteen pixels took this Gaussian: each adds its own values (cheaper
                     // than the warp reduction below at these counts)
                     if (has) {
-                        float* row = A.work + (size_t)s_id[k] * kWorkRow;
+                        float* row = A.work + (size_t)s_id[k] * kRow;
                         atomicAdd(reinterpret_cast<float4*>(row), make_float4(v[0], v[1], v[2], v[3]));
                         atomicAdd(reinterpret_cast<float4*>(row + 4), make_float4(v[4], v[5], v[6], v[7]));
-                        atomicAdd(reinterpret_cast<float2*>(row + 8), make_float2(v[8], v[9]));
+                        if (kPup) {
+                            atomicAdd(reinterpret_cast<float4*>(row + 8), make_float4(v[8], v[9], v[10], v[11]));
+                            atomicAdd(reinterpret_cast<float4*>(row + 12), make_float4(v[12], v[13], v[14], 0.0f));
+                        } else {
+                            atomicAdd(reinterpret_cast<float2*>(row + 8), make_float2(v[8], v[9]));
+                        }
                     }
                 } else if (hm != 0u) {
                     // Warp sum of the 10 values by halving exchanges: after
@@ -169,7 +201,7 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_
                     // atomic each.
                     float w[16];
 #pragma unroll
-                    for (int m = 0; m < 16; ++m) w[m] = (m < kWork && has) ? v[m < kWork ? m : 0] : 0.0f;
+                    for (int m = 0; m < 16; ++m) w[m] = (m < kNV && has) ? v[m] : 0.0f;
                     const bool up16 = (lane & 16) != 0;
 #pragma unroll
                     for (int m = 0; m < 8; ++m) {
@@ -188,10 +220,12 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_
                     for (int off = 4; off > 0; off >>= 1)
 #pragma unroll
                         for (int m = 0; m < 4; ++m) w[m] += __shfl_xor_sync(0xffffffffu, w[m], off);
-                    float* row = A.work + (size_t)s_id[k] * kWorkRow;
+                    float* row = A.work + (size_t)s_id[k] * kRow;
                     if (lane == 0) atomicAdd(reinterpret_cast<float4*>(row), make_float4(w[0], w[1], w[2], w[3]));
                     else if (lane == 8) atomicAdd(reinterpret_cast<float4*>(row + 4), make_float4(w[0], w[1], w[2], w[3]));
-                    else if (lane == 16) atomicAdd(reinterpret_cast<float2*>(row + 8), make_float2(w[0], w[1]));
+                    else if (kPup && lane == 16) atomicAdd(reinterpret_cast<float4*>(row + 8), make_float4(w[0], w[1], w[2], w[3]));
+                    else if (kPup && lane == 24) atomicAdd(reinterpret_cast<float4*>(row + 12), make_float4(w[0], w[1], w[2], w[3]));
+                    else if (!kPup && lane == 16) atomicAdd(reinterpret_cast<float2*>(row + 8), make_float2(w[0], w[1]));
                 }
             }
         }
@@ -270,6 +304,119 @@ __device__ void sh_eval(float x, float y, float z, float Y[16], float dY[16][3])
         for (int j = 0; j < 3; ++j) dY[k][j] = g[k][j];
 }
 
+// Projection of one Gaussian as the backward chain needs it (Sec. 3.2.1):
+// view-space mean, normalised quaternion and rotation, M = R S, Sigma3D,
+// T = J W and the 2D covariance, with the x/z, y/z clamp state.
+struct ProjChain {
+    float x, y, z, tx, ty, nq;
+    bool clx, cly;
+    float qn[4];
+    float Rm[3][3], M[3][3], S3[3][3], T[2][3], TS[2][3];
+    float sxx, sxy, syy;
+};
+
+__device__ __forceinline__ void chain_setup(ProjChain& P, const float* V, float fx, float fy, float limx, float limy,
+                                            const float mu[3], const float sc[3], const float q[4]) {
+    float p[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) p[r] = V[4 * r] * mu[0] + V[4 * r + 1] * mu[1] + V[4 * r + 2] * mu[2] + V[4 * r + 3];
+    P.x = p[0], P.y = p[1], P.z = p[2];
+    P.nq = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const float qw = q[0] / P.nq, qx = q[1] / P.nq, qy = q[2] / P.nq, qz = q[3] / P.nq;
+    P.qn[0] = qw, P.qn[1] = qx, P.qn[2] = qy, P.qn[3] = qz;
+    const float R[3][3] = {{1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
+                           {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
+                           {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            P.Rm[r][k] = R[r][k];
+            P.M[r][k] = R[r][k] * sc[k];
+        }
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            P.S3[r][c] = P.M[r][0] * P.M[c][0] + P.M[r][1] * P.M[c][1] + P.M[r][2] * P.M[c][2];
+    const float z = P.z;
+    const float xz = P.x / z, yz = P.y / z;
+    P.clx = xz < -limx || xz > limx;
+    P.cly = yz < -limy || yz > limy;
+    P.tx = fminf(limx, fmaxf(-limx, xz)) * z;
+    P.ty = fminf(limy, fmaxf(-limy, yz)) * z;
+    const float z2 = z * z;
+    const float J[2][3] = {{fx / z, 0.0f, -fx * P.tx / z2}, {0.0f, fy / z, -fy * P.ty / z2}};
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) P.T[r][k] = J[r][0] * V[k] + J[r][1] * V[4 + k] + J[r][2] * V[8 + k];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            P.TS[r][c] = P.T[r][0] * P.S3[0][c] + P.T[r][1] * P.S3[1][c] + P.T[r][2] * P.S3[2][c];
+    P.sxx = P.TS[0][0] * P.T[0][0] + P.TS[0][1] * P.T[0][1] + P.TS[0][2] * P.T[0][2] + 0.3f;
+    P.sxy = P.TS[0][0] * P.T[1][0] + P.TS[0][1] * P.T[1][1] + P.TS[0][2] * P.T[1][2];
+    P.syy = P.TS[1][0] * P.T[1][0] + P.TS[1][1] * P.T[1][1] + P.TS[1][2] * P.T[1][2] + 0.3f;
+}
+
+// Chain from gradients with respect to (u, v) and the conic (a, b, c) to
+// the mean (dmu, through the projection and the Jacobian J) and to M = R S
+// (dM, from which the scale and rotation gradients follow).
+__device__ __forceinline__ void chain_apply(const ProjChain& P, const float* V, float fx, float fy, float gu, float gv,
+                                            float ga, float gb, float gc, float dmu[3], float dM[3][3]) {
+    const float x = P.x, y = P.y, z = P.z, tx = P.tx, ty = P.ty;
+    const float z2 = z * z, z3 = z2 * z;
+    const float sxx = P.sxx, sxy = P.sxy, syy = P.syy;
+    const float det = sxx * syy - sxy * sxy;
+    const float id = 1.0f / det, id2 = id * id;
+    const float g_sxx = ga * (-syy * syy * id2) + gb * (sxy * syy * id2) + gc * (id - sxx * syy * id2);
+    const float g_syy = ga * (id - sxx * syy * id2) + gb * (sxy * sxx * id2) + gc * (-sxx * sxx * id2);
+    const float g_sxy = ga * (2.0f * sxy * syy * id2) + gb * (-id - 2.0f * sxy * sxy * id2) + gc * (2.0f * sxy * sxx * id2);
+    const float G2[2][2] = {{g_sxx, 0.5f * g_sxy}, {0.5f * g_sxy, g_syy}};
+    float G3[3][3], dT[2][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            G3[r][c] = P.T[0][r] * (G2[0][0] * P.T[0][c] + G2[0][1] * P.T[1][c]) +
+                       P.T[1][r] * (G2[1][0] * P.T[0][c] + G2[1][1] * P.T[1][c]);
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) dT[r][c] = 2.0f * (G2[r][0] * P.TS[0][c] + G2[r][1] * P.TS[1][c]);
+    float dJ[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dJ[r][k] = dT[r][0] * V[4 * k] + dT[r][1] * V[4 * k + 1] + dT[r][2] * V[4 * k + 2];
+    float dp[3] = {0.0f, 0.0f, 0.0f};
+    dp[2] += dJ[0][0] * (-fx / z2) + dJ[1][1] * (-fy / z2);
+    if (!P.clx) {
+        dp[0] += dJ[0][2] * (-fx / z2);
+        dp[2] += dJ[0][2] * (2.0f * fx * x / z3);
+    } else {
+        dp[2] += dJ[0][2] * (fx * (tx / z) / z2);
+    }
+    if (!P.cly) {
+        dp[1] += dJ[1][2] * (-fy / z2);
+        dp[2] += dJ[1][2] * (2.0f * fy * y / z3);
+    } else {
+        dp[2] += dJ[1][2] * (fy * (ty / z) / z2);
+    }
+    dp[0] += gu * fx / z;
+    dp[1] += gv * fy / z;
+    dp[2] += gu * (-fx * x / z2) + gv * (-fy * y / z2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dmu[k] = V[k] * dp[0] + V[4 + k] * dp[1] + V[8 + k] * dp[2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            dM[r][k] = 2.0f * (G3[r][0] * P.M[0][k] + G3[r][1] * P.M[1][k] + G3[r][2] * P.M[2][k]);
+}
+
 __global__ void __launch_bounds__(256, 4) preprocess_backward_kernel(const PreBwdArgs A) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n) return;
@@ -300,90 +447,12 @@ __global__ void __launch_bounds__(256, 4) preprocess_backward_kernel(const PreBw
     const float mu[3] = {A.means[i], A.means[n + i], A.means[2 * n + i]};
     const float sc[3] = {A.scales[i], A.scales[n + i], A.scales[2 * n + i]};
     const float q[4] = {A.rots[i], A.rots[n + i], A.rots[2 * n + i], A.rots[3 * n + i]};
-    const float* V = A.V;
-    float p[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) p[r] = V[4 * r] * mu[0] + V[4 * r + 1] * mu[1] + V[4 * r + 2] * mu[2] + V[4 * r + 3];
-    const float x = p[0], y = p[1], z = p[2];
-    const float nq = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
-    const float qw = q[0] / nq, qx = q[1] / nq, qy = q[2] / nq, qz = q[3] / nq;
-    const float Rm[3][3] = {{1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)},
-                            {2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)},
-                            {2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)}};
-    float M[3][3], S3[3][3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) M[r][k] = Rm[r][k] * sc[k];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) S3[r][c] = M[r][0] * M[c][0] + M[r][1] * M[c][1] + M[r][2] * M[c][2];
-    const float xz = x / z, yz = y / z;
-    const bool clx = xz < -A.limx || xz > A.limx, cly = yz < -A.limy || yz > A.limy;
-    const float tx = fminf(A.limx, fmaxf(-A.limx, xz)) * z, ty = fminf(A.limy, fmaxf(-A.limy, yz)) * z;
-    const float z2 = z * z, z3 = z2 * z;
-    const float J[2][3] = {{A.fx / z, 0.0f, -A.fx * tx / z2}, {0.0f, A.fy / z, -A.fy * ty / z2}};
-    float T[2][3], TS[2][3];
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) T[r][k] = J[r][0] * V[k] + J[r][1] * V[4 + k] + J[r][2] * V[8 + k];
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) TS[r][c] = T[r][0] * S3[0][c] + T[r][1] * S3[1][c] + T[r][2] * S3[2][c];
-    const float sxx = TS[0][0] * T[0][0] + TS[0][1] * T[0][1] + TS[0][2] * T[0][2] + 0.3f;
-    const float sxy = TS[0][0] * T[1][0] + TS[0][1] * T[1][1] + TS[0][2] * T[1][2];
-    const float syy = TS[1][0] * T[1][0] + TS[1][1] * T[1][1] + TS[1][2] * T[1][2] + 0.3f;
-    const float det = sxx * syy - sxy * sxy;
-    const float id = 1.0f / det, id2 = id * id;
-    const float ga = gr[2], gb = gr[3], gc = gr[4];
-    const float g_sxx = ga * (-syy * syy * id2) + gb * (sxy * syy * id2) + gc * (id - sxx * syy * id2);
-    const float g_syy = ga * (id - sxx * syy * id2) + gb * (sxy * sxx * id2) + gc * (-sxx * sxx * id2);
-    const float g_sxy = ga * (2.0f * sxy * syy * id2) + gb * (-id - 2.0f * sxy * sxy * id2) + gc * (2.0f * sxy * sxx * id2);
-    const float G2[2][2] = {{g_sxx, 0.5f * g_sxy}, {0.5f * g_sxy, g_syy}};
-    float G3[3][3], dT[2][3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            G3[r][c] = T[0][r] * (G2[0][0] * T[0][c] + G2[0][1] * T[1][c]) +
-                       T[1][r] * (G2[1][0] * T[0][c] + G2[1][1] * T[1][c]);
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) dT[r][c] = 2.0f * (G2[r][0] * TS[0][c] + G2[r][1] * TS[1][c]);
-    float dJ[2][3];
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) dJ[r][k] = dT[r][0] * V[4 * k] + dT[r][1] * V[4 * k + 1] + dT[r][2] * V[4 * k + 2];
-    float dp[3] = {0.0f, 0.0f, 0.0f};
-    dp[2] += dJ[0][0] * (-A.fx / z2) + dJ[1][1] * (-A.fy / z2);
-    if (!clx) {
-        dp[0] += dJ[0][2] * (-A.fx / z2);
-        dp[2] += dJ[0][2] * (2.0f * A.fx * x / z3);
-    } else {
-        dp[2] += dJ[0][2] * (A.fx * (tx / z) / z2);
-    }
-    if (!cly) {
-        dp[1] += dJ[1][2] * (-A.fy / z2);
-        dp[2] += dJ[1][2] * (2.0f * A.fy * y / z3);
-    } else {
-        dp[2] += dJ[1][2] * (A.fy * (ty / z) / z2);
-    }
-    dp[0] += gr[0] * A.fx / z;
-    dp[1] += gr[1] * A.fy / z;
-    dp[2] += gr[0] * (-A.fx * x / z2) + gr[1] * (-A.fy * y / z2);
-    float dmu[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) dmu[k] = V[k] * dp[0] + V[4 + k] * dp[1] + V[8 + k] * dp[2];
-    float dM[3][3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) dM[r][k] = 2.0f * (G3[r][0] * M[0][k] + G3[r][1] * M[1][k] + G3[r][2] * M[2][k]);
+    ProjChain P;
+    chain_setup(P, A.V, A.fx, A.fy, A.limx, A.limy, mu, sc, q);
+    const float nq = P.nq, qw = P.qn[0], qx = P.qn[1], qy = P.qn[2], qz = P.qn[3];
+    float dmu[3], dM[3][3];
+    chain_apply(P, A.V, A.fx, A.fy, gr[0], gr[1], gr[2], gr[3], gr[4], dmu, dM);
+    const auto& Rm = P.Rm;
     float dR[3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -431,9 +500,180 @@ __global__ void __launch_bounds__(256, 4) preprocess_backward_kernel(const PreBw
     for (int k = 0; k < 3; ++k) A.g_means[k * n + i] = dmu[k] + (ddir[k] - dir[k] * dd) / len;
 }
 
+
+// ---------------------------------------------------------------- PUP sensitivity (Sec. 4.2, Eq. pup_score)
+// H_i = sum over views, pixels and channels of grad_{mu,s} C grad_{mu,s} C^T,
+// through the 2D Gaussian value g_i(p): grad_{mu,s} C_ch(p) =
+// dC_ch/dg * J_i^T G5(p), with G5 = dg/d(u, v, a, b, c) and J_i the 5 x 6
+// Jacobian of (u, v, a, b, c) with respect to (mu, s).  So
+// H_i += J_i^T (sum_p w_p G5 G5^T) J_i per view; the blend pass above sums the
+// 5 x 5 matrix, this pass applies J_i (its five rows are the projection chain
+// applied to unit gradients) and adds the 21 entries of the symmetric 6 x 6
+// matrix to hessian[21][n] (row-major upper triangle, order mu_x mu_y mu_z
+// s_0 s_1 s_2).
+struct PupArgs {
+    const float* means;
+    const float* scales;
+    const float* rots;
+    const int32_t* counts;
+    const float* work;  // [ncap][16]
+    int64_t n;
+    float fx, fy, limx, limy;
+    float V[12];
+    float* hessian;     // [21][n], +=
+};
+
+__global__ void __launch_bounds__(256) pup_jacobian_kernel(const PupArgs A) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n || A.counts[i] <= 0) return;
+    const int64_t n = A.n;
+    float M5[5][5];
+    {
+        const float* row = A.work + (size_t)i * 16;
+        int m = 0;
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+            for (int c = r; c < 5; ++c) {
+                M5[r][c] = row[m];
+                M5[c][r] = row[m];
+                ++m;
+            }
+    }
+    const float mu[3] = {A.means[i], A.means[n + i], A.means[2 * n + i]};
+    const float sc[3] = {A.scales[i], A.scales[n + i], A.scales[2 * n + i]};
+    const float q[4] = {A.rots[i], A.rots[n + i], A.rots[2 * n + i], A.rots[3 * n + i]};
+    ProjChain P;
+    chain_setup(P, A.V, A.fx, A.fy, A.limx, A.limy, mu, sc, q);
+    float Jt[5][6];  // row k: d(2D parameter k)/d(mu, s)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        float dmu[3], dM[3][3];
+        chain_apply(P, A.V, A.fx, A.fy, k == 0 ? 1.0f : 0.0f, k == 1 ? 1.0f : 0.0f, k == 2 ? 1.0f : 0.0f,
+                    k == 3 ? 1.0f : 0.0f, k == 4 ? 1.0f : 0.0f, dmu, dM);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Jt[k][a] = dmu[a];
+            Jt[k][3 + a] = dM[0][a] * P.Rm[0][a] + dM[1][a] * P.Rm[1][a] + dM[2][a] * P.Rm[2][a];
+        }
+    }
+    float MJ[5][6];  // M5 Jt
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int b = 0; b < 6; ++b) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int l = 0; l < 5; ++l) acc += M5[k][l] * Jt[l][b];
+            MJ[k][b] = acc;
+        }
+    int e = 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int b = a; b < 6; ++b) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) acc += Jt[k][a] * MJ[k][b];
+            A.hessian[(int64_t)e * n + i] += acc;
+            ++e;
+        }
+}
+
+// U_i = log det H_i by a Cholesky factorisation in double precision; -inf
+// where H_i is not positive definite (e.g. a Gaussian seen from one view
+// only: its 6 x 6 block has rank 5 at most).
+__global__ void __launch_bounds__(256) pup_logdet_kernel(const float* __restrict__ hessian, int64_t n,
+                                                        float* __restrict__ score) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double H[6][6];
+    int e = 0;
+    for (int a = 0; a < 6; ++a)
+        for (int b = a; b < 6; ++b) {
+            H[a][b] = H[b][a] = (double)hessian[(int64_t)e * n + i];
+            ++e;
+        }
+    double logdet = 0.0;
+    bool pd = true;
+    for (int j = 0; j < 6 && pd; ++j) {
+        double d = H[j][j];
+        for (int k = 0; k < j; ++k) d -= H[j][k] * H[j][k];
+        if (!(d > 0.0)) {
+            pd = false;
+            break;
+        }
+        const double l = sqrt(d);
+        H[j][j] = l;
+        logdet += 2.0 * log(l);
+        for (int r = j + 1; r < 6; ++r) {
+            double v = H[r][j];
+            for (int k = 0; k < j; ++k) v -= H[r][k] * H[j][k];
+            H[r][j] = v / l;
+        }
+    }
+    score[i] = pd ? (float)logdet : -INFINITY;
+}
+
 }  // namespace
 
 int64_t backward_work_floats(int64_t ncap) { return (int64_t)kWorkRow * ncap; }
+
+gs_status launch_pup(gs_context* ctx, const gs_scene* s, const gs_camera* cam, const gs_raster_cfg* cfg,
+                     const FrameView& v, float* hessian, float* work) {
+    if (cudaMemsetAsync(work, 0, (size_t)v.ncap * 16 * sizeof(float), ctx->stream) != cudaSuccess)
+        return set_error(ctx, GS_ERR_CUDA, "pup: cudaMemsetAsync(work) failed");
+    BwdArgs B{};
+    B.ranges = v.ranges;
+    B.vals = v.vals0;
+    B.p0 = v.p0;
+    B.p1 = v.p1;
+    B.p2 = v.p2;
+    B.final_T = v.final_T;
+    B.last = v.last;
+    B.dL_dimg = nullptr;
+    B.work = work;
+    B.ncap = v.ncap;
+    B.width = v.width;
+    B.height = v.height;
+    B.gx = v.gx;
+    B.bg0 = cfg->bg[0];
+    B.bg1 = cfg->bg[1];
+    B.bg2 = cfg->bg[2];
+    const unsigned tiles = (unsigned)(v.gx * v.gy);
+    switch (v.tile) {
+        case 8: blend_backward_kernel<8, true><<<tiles, 64, 0, ctx->stream>>>(B); break;
+        case 16: blend_backward_kernel<16, true><<<tiles, 256, 0, ctx->stream>>>(B); break;
+        case 32: blend_backward_kernel<32, true><<<tiles, 1024, 0, ctx->stream>>>(B); break;
+        default: return set_error(ctx, GS_ERR_INVALID, "pup: tile %d not supported", v.tile);
+    }
+    ctx->launches += 1;
+    gs_status st = check_launch(ctx, "pup blend");
+    if (st || s->n == 0) return st;
+    PupArgs P;
+    P.means = s->means;
+    P.scales = s->scales;
+    P.rots = s->rotations;
+    P.counts = v.counts;
+    P.work = work;
+    P.n = s->n;
+    P.fx = cam->fx;
+    P.fy = cam->fy;
+    P.limx = 1.3f * cam->tan_fovx;
+    P.limy = 1.3f * cam->tan_fovy;
+    for (int k = 0; k < 12; ++k) P.V[k] = cam->viewmat[k];
+    P.hessian = hessian;
+    pup_jacobian_kernel<<<(unsigned)((s->n + 255) / 256), 256, 0, ctx->stream>>>(P);
+    ctx->launches += 1;
+    return check_launch(ctx, "pup jacobian");
+}
+
+gs_status launch_pup_score(gs_context* ctx, const float* hessian, int64_t n, float* score) {
+    if (n == 0) return GS_OK;
+    pup_logdet_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(hessian, n, score);
+    ctx->launches += 1;
+    return check_launch(ctx, "pup logdet");
+}
 
 gs_status launch_backward(gs_context* ctx, const gs_scene* s, const gs_camera* cam, const gs_raster_cfg* cfg,
                           const FrameView& v, const float* dL_dimg, const gs_grads* g) {
@@ -459,9 +699,9 @@ gs_status launch_backward(gs_context* ctx, const gs_scene* s, const gs_camera* c
     B.bg2 = cfg->bg[2];
     const unsigned tiles = (unsigned)(v.gx * v.gy);
     switch (v.tile) {
-        case 8: blend_backward_kernel<8><<<tiles, 64, 0, ctx->stream>>>(B); break;
-        case 16: blend_backward_kernel<16><<<tiles, 256, 0, ctx->stream>>>(B); break;
-        case 32: blend_backward_kernel<32><<<tiles, 1024, 0, ctx->stream>>>(B); break;
+        case 8: blend_backward_kernel<8, false><<<tiles, 64, 0, ctx->stream>>>(B); break;
+        case 16: blend_backward_kernel<16, false><<<tiles, 256, 0, ctx->stream>>>(B); break;
+        case 32: blend_backward_kernel<32, false><<<tiles, 1024, 0, ctx->stream>>>(B); break;
         default: return set_error(ctx, GS_ERR_INVALID, "render_backward: tile %d not supported", v.tile);
     }
     ctx->launches += 1;

@@ -297,4 +297,7 @@ gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameVi
 gs_status launch_backward(gs_context* ctx, const gs_scene* s, const gs_camera* cam, const gs_raster_cfg* cfg,
                           const FrameView& v, const float* dL_dimg, const gs_grads* g);
 int64_t backward_work_floats(int64_t ncap);
+gs_status launch_pup(gs_context* ctx, const gs_scene* s, const gs_camera* cam, const gs_raster_cfg* cfg,
+                     const FrameView& v, float* hessian, float* work);
+gs_status launch_pup_score(gs_context* ctx, const float* hessian, int64_t n, float* score);
 }  // namespace gs

@@ -72,7 +72,8 @@ class GsFrameBytes(ctypes.Structure):
 EXPORTS = ["gs_create", "gs_destroy", "gs_set_stream", "gs_last_error", "gs_launch_count", "gs_frame_sizes",
            "gs_preprocess", "gs_intersect", "gs_sort", "gs_tile_ranges", "gs_render", "gs_render_stats",
            "gs_forward", "gs_read_status", "gs_backward_work_bytes", "gs_render_backward", "gs_intersect_noalloc",
-           "gs_batch_sizes", "gs_forward_batch", "gs_batch_status", "gs_read_culled", "gs_set_sort_wait"]
+           "gs_batch_sizes", "gs_forward_batch", "gs_batch_status", "gs_read_culled", "gs_set_sort_wait",
+           "gs_pup_work_bytes", "gs_pup_accumulate", "gs_pup_score"]
 
 _lib = None
 
@@ -112,12 +113,16 @@ def load(path=None) -> ctypes.CDLL:
     L.gs_intersect_noalloc.argtypes = [P, POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame),
                                        POINTER(c_int64)]
     L.gs_read_culled.argtypes = [P, POINTER(GsFrame), POINTER(c_int64)]
+    L.gs_pup_work_bytes.argtypes = [c_int64]
+    L.gs_pup_accumulate.argtypes = [P, POINTER(GsScene), POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame), P, P]
+    L.gs_pup_score.argtypes = [P, P, c_int64, P]
     L.gs_set_sort_wait.argtypes = [P, c_uint32, c_int64]
     L.gs_render_backward.argtypes = [P, POINTER(GsScene), POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame),
                                      P, POINTER(GsGrads)]
     for name in EXPORTS:
         getattr(L, name).restype = ctypes.c_int
     L.gs_backward_work_bytes.restype = c_int64
+    L.gs_pup_work_bytes.restype = c_int64
     L.gs_destroy.restype = None
     L.gs_last_error.restype = ctypes.c_char_p
     L.gs_launch_count.restype = c_int64
@@ -320,6 +325,18 @@ class Rasterizer:
                                                 ctypes.byref(frame.struct), c_void_p(dL_dimage.data_ptr()),
                                                 ctypes.byref(g)), "gs_render_backward")
 
+    def gs_pup_accumulate(self, scene, cam, cfg, frame: Frame, hessian: torch.Tensor, work: torch.Tensor):
+        """Adds one view's PUP sensitivity terms to hessian ([21, n] float32,
+        device) for the frame's completed forward render."""
+        s, c = scene_struct(scene), camera_struct(cam)
+        self._check(self.lib.gs_pup_accumulate(self.ctx, ctypes.byref(s), ctypes.byref(c), ctypes.byref(cfg),
+                                               ctypes.byref(frame.struct), c_void_p(hessian.data_ptr()),
+                                               c_void_p(work.data_ptr())), "gs_pup_accumulate")
+
+    def gs_pup_score(self, hessian: torch.Tensor, n: int, score: torch.Tensor):
+        self._check(self.lib.gs_pup_score(self.ctx, c_void_p(hessian.data_ptr()), int(n), c_void_p(score.data_ptr())),
+                    "gs_pup_score")
+
     def gs_forward(self, scene, cam, cfg, frame: Frame):
         s, c = scene_struct(scene), camera_struct(cam)
         self._check(self.lib.gs_forward(self.ctx, ctypes.byref(s), ctypes.byref(c), ctypes.byref(cfg),
@@ -411,6 +428,26 @@ class Renderer:
 
 def backward_work_bytes(n: int) -> int:
     return int(load().gs_backward_work_bytes(int(n)))
+
+
+def pup_work_bytes(n: int) -> int:
+    return int(load().gs_pup_work_bytes(int(n)))
+
+
+def pup_scores(renderer: "Renderer", scene, cams, mode="accutile", tile=16, bg=(0.0, 0.0, 0.0)):
+    """PUP sensitivity over the views ``cams``: returns (hessian [21, n],
+    score [n] = log det H_i) as device tensors."""
+    n = int(scene.means.shape[1])
+    dev = scene.means.device
+    H = torch.zeros(21, n, dtype=torch.float32, device=dev)
+    work = torch.empty(max(pup_work_bytes(n) // 4, 4), dtype=torch.float32, device=dev)
+    cfg = cfg_struct(tile, mode, bg)
+    for cam in cams:
+        out = renderer.render(scene, cam, mode, tile, bg)
+        renderer.rast.gs_pup_accumulate(scene, cam, cfg, out.frame, H, work)
+    score = torch.empty(n, dtype=torch.float32, device=dev)
+    renderer.rast.gs_pup_score(H, n, score)
+    return H, score
 
 
 class SceneView:
