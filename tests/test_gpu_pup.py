@@ -46,7 +46,9 @@ def test_pup_hessian_and_logdet_against_oracle(raster, mode, tile):
     # log det where the block is well conditioned
     M = oracle.pup_full(ref)
     ev = np.linalg.eigvalsh(M)
-    good = (ev[:, 0] > 0) & (ev[:, -1] < 1e4 * ev[:, 0])
+    # (the FP32 sums carry a relative error near 1e-6 of the block's largest
+    # eigenvalue, so log det is compared where the condition number is < 1e3)
+    good = (ev[:, 0] > 0) & (ev[:, -1] < 1e3 * ev[:, 0])
     assert good.sum() > 100
     want = np.linalg.slogdet(M[good])[1]
     assert np.abs(score[good] - want).max() <= 1e-2
