@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-backward", action="store_true")
     p.add_argument("--no-configs", action="store_true", help="skip the 16k-box and 300k-prune mode tables")
+    p.add_argument("--no-pruning", action="store_true", help="skip the Soft/Hard pruning and PUP-score experiments")
+    p.add_argument("--prune-scale", type=float, default=0.1, help="pruning schedule length relative to 30k iterations")
     p.add_argument("--serve-duration", type=float, default=10.0, help="seconds of arrivals per rate")
     p.add_argument("--serve-rates", default="200,500,1000,2000")
     a = p.parse_args()
@@ -557,6 +559,18 @@ def run_ours(args):
     if not args.no_serve and rank == 0:
         served = run_serving(args, dev, scene)
 
+    pruning = None
+    if not args.no_pruning and rank == 0:
+        from paper_2412_00578_gb300 import prune
+
+        sch = prune.Schedule(scale=args.prune_scale)
+        task = prune.make_task(dev)
+        pruning = {"task": "fit 16 seeded views (256x192) of a 20k-Gaussian box scene from a 40k-Gaussian "
+                           "over-complete start; L1 + D-SSIM, Adam, 3D-GS densification and opacity resets; "
+                           f"iteration counts x{args.prune_scale} of the paper's 30k",
+                   "soft_hard": prune.run_schedule(dev, sch, task),
+                   "pup_vs_efficient": prune.run_pup_vs_efficient(dev, sch, task)}
+
     if rank == 0:
         fps = world * 1e3 / ms_acc
         emit({"metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -569,7 +583,7 @@ def run_ours(args):
               "stages_ms": stages, "stage_roofline": stage_frac, "frame_roofline": frame_roof,
               "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
               "cpu_baseline": cpu, "backward": backward, "configs": configs, "multiview": multiview,
-              "served": served})
+              "served": served, "pruning": pruning})
     if world > 1:
         dist.destroy_process_group()
 
@@ -732,8 +746,22 @@ def run_backward(args, raster, rast, scene, cam, cfg, frame, stream, max_over_ra
         rast.gs_render_backward(scene, cam, cfg, frame, dL, grads, work)
 
     ms_fb = timed_loop(step)
+    # PUP's sensitivity for the same view (its 5x5 blend sums, Jacobian pass
+    # and log det), against the efficient score that comes with the backward
+    H = torch.zeros(21, n, dtype=torch.float32, device=dev)
+    pwork = torch.empty(max(raster.pup_work_bytes(n) // 4, 4), dtype=torch.float32, device=dev)
+    pscore = torch.empty(n, dtype=torch.float32, device=dev)
+    rast.gs_forward(scene, cam, cfg, frame)
+
+    def pup_step():
+        rast.gs_pup_accumulate(scene, cam, cfg, frame, H, pwork)
+        rast.gs_pup_score(H, n, pscore)
+
+    ms_pup = timed_loop(pup_step)
     return {"workload": f"{WORKLOAD} AccuTile frame, dL/dimage ~ N(0, 1)", "steps": steps,
             "ms_backward": ms_b, "ms_forward_plus_backward": ms_fb,
+            "ms_pup_sensitivity_one_view": ms_pup,
+            "score_bytes_per_gaussian": {"efficient": 4, "pup_hessian": 84, "pup_work": 64, "backward_work": 48},
             "kernels": "memset, blend_backward<16>, preprocess_backward",
             "gaussians_with_score": int((grads["score"] > 0).sum().item())}
 
