@@ -1,7 +1,10 @@
 """Autotuner for multi-view batches: picks the tile edge (8, 16, 32) and the
-radix sort's digit width (8-bit or 6-bit digits) by timing the actual batch
-with CUDA events, and caches the choice per (device, Gaussian-count bucket,
-pixel-count bucket, camera count, mode).
+radix sort's digit width (4 to 8 bits) by timing the actual batch with CUDA
+events, and caches the choice per (device, Gaussian-count bucket,
+pixel-count bucket, camera count, mode).  The tile edge also fixes the block
+shape of the blend and its backward (one thread per pixel: 64, 256 or 1024
+threads per CTA, 8 x 4-pixel warp sub-tiles), so the 15 candidates cover
+tile x threads per tile x digit width.
 
 In the exact modes (SnugBox, AccuTile) the image does not depend on the tile
 edge or on the digit width, so the choice changes speed only.
@@ -17,7 +20,7 @@ import torch
 
 from . import raster
 
-CANDIDATES = [(t, d) for t in (8, 16, 32) for d in (0, 6)]
+CANDIDATES = [(t, d) for t in (8, 16, 32) for d in (0, 7, 6, 5, 4)]  # d = 0: 8-bit digits
 CACHE = Path(__file__).resolve().parent / "_build" / "autotune.json"
 
 

@@ -132,6 +132,7 @@ bool make_view(gs_context* ctx, const gs_frame* f, FrameView* v, unsigned need) 
     v->sort_lookback = reinterpret_cast<uint32_t*>(s + L.lookback);
     v->sort_partitions = std::max<int64_t>(sort_partitions_for(f->key_capacity), 1);
     v->tile_order = reinterpret_cast<uint32_t*>(s + L.order);
+    v->tile_order_cap = kMaxOrderedTiles;
     if ((reinterpret_cast<uintptr_t>(f->proj) & 15) || (reinterpret_cast<uintptr_t>(f->keys) & 7) ||
         (reinterpret_cast<uintptr_t>(f->ranges) & 7) || (reinterpret_cast<uintptr_t>(f->scratch) & 15)) {
         set_error(ctx, GS_ERR_INVALID, "frame buffer misaligned (proj/scratch need 16 B, keys/ranges 8 B)");

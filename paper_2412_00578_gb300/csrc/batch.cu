@@ -13,14 +13,18 @@ int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct BatchLayout {
     ScratchLayout base;
-    int64_t table, total;
+    int64_t table, order, ctl, total;
 };
 
-BatchLayout batch_layout(int64_t n_capacity, int64_t max_cams, int64_t kcap) {
+// The batch scratch adds the camera table, a launch order for all of the
+// batch's tiles and the counters of the multi-block ordering.
+BatchLayout batch_layout(int64_t n_capacity, int64_t max_cams, int64_t kcap, int64_t tile_capacity) {
     BatchLayout L;
     L.base = scratch_layout(n_capacity * max_cams, kcap);
     L.table = L.base.total;
-    L.total = L.table + align_up(max_cams * (int64_t)sizeof(CamRec));
+    L.order = L.table + align_up(max_cams * (int64_t)sizeof(CamRec));
+    L.ctl = L.order + align_up(tile_capacity * 4);
+    L.total = L.ctl + align_up(67 * 4);
     return L;
 }
 
@@ -116,7 +120,7 @@ bool make_batch_view(gs_context* ctx, const gs_batch_frame* f, int num_cams, Fra
     v->image = f->image;
     v->final_T = f->final_T;
     v->last = f->last;
-    const BatchLayout L = batch_layout(f->n_capacity, f->max_cams, f->key_capacity);
+    const BatchLayout L = batch_layout(f->n_capacity, f->max_cams, f->key_capacity, f->tile_capacity);
     unsigned char* s = static_cast<unsigned char*>(f->scratch);
     v->status = reinterpret_cast<uint32_t*>(s + L.base.status);
     v->scan_partials = reinterpret_cast<long long*>(s + L.base.partials);
@@ -124,7 +128,9 @@ bool make_batch_view(gs_context* ctx, const gs_batch_frame* f, int num_cams, Fra
     v->sort_ticket = v->sort_hist + kMaxPasses * 256;
     v->sort_lookback = reinterpret_cast<uint32_t*>(s + L.base.lookback);
     v->sort_partitions = std::max<int64_t>(sort_partitions_for(f->key_capacity), 1);
-    v->tile_order = reinterpret_cast<uint32_t*>(s + L.base.order);
+    v->tile_order = reinterpret_cast<uint32_t*>(s + L.order);
+    v->tile_order_cap = f->tile_capacity;
+    v->order_ctl = reinterpret_cast<uint32_t*>(s + L.ctl);
     v->table = reinterpret_cast<const CamRec*>(s + L.table);
     v->num_cams = num_cams;
     v->cam_stride = f->n_capacity;
@@ -158,7 +164,7 @@ gs_status gs_batch_sizes(int64_t n_capacity, int32_t max_cams, int32_t tile, int
     out->image = 3 * pixel_capacity * 4;
     out->final_T = pixel_capacity * 4;
     out->last = pixel_capacity * 4;
-    out->scratch = batch_layout(n_capacity, max_cams, key_capacity).total;
+    out->scratch = batch_layout(n_capacity, max_cams, key_capacity, tile_capacity).total;
     return GS_OK;
 }
 

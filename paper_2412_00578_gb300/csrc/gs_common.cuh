@@ -73,7 +73,9 @@ struct FrameView {
     uint32_t* sort_ticket;     // [kMaxPasses]
     uint32_t* sort_lookback;   // [2][sort_partitions][256] look-back words, see sort.cu
     int64_t sort_partitions;   // partitions the look-back table holds
-    uint32_t* tile_order;      // [kMaxOrderedTiles] the blend's tile launch order
+    uint32_t* tile_order;      // [tile_order_cap] the blend's tile launch order
+    int64_t tile_order_cap = 0;
+    uint32_t* order_ctl = nullptr;  // [67] class counts, class bases, done counter (multi-block ordering)
     // multi-view batches only (table == nullptr for a single camera)
     const CamRec* table = nullptr;
     int num_cams = 1;

@@ -20,6 +20,8 @@
 // pixel stops before adding it; else C = fma(c, alpha T, C), T = T'.
 // The CTA leaves the loop as soon as every pixel has stopped
 // (__syncthreads_count vote before each batch).
+#include <algorithm>
+
 #include "blend_common.cuh"
 
 namespace gs {
@@ -155,6 +157,62 @@ __global__ void __launch_bounds__(1024) tile_order_kernel(const uint2* __restric
         const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
         uint32_t b = 0;
         if (t < tiles && lane == leader) b = atomicAdd(&base[cls], (uint32_t)__popc(peers));
+        b = __shfl_sync(0xffffffffu, b, leader);
+        if (t < tiles) order[b + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = t;
+    }
+}
+
+// The same heaviest-first order for more tiles than one block holds (a
+// multi-view batch): many blocks count the tiles per class (shared-memory
+// counters, one global atomic per class and block); the last block to finish
+// turns the counts into class bases; a second launch places every tile in
+// its class's segment (warp-aggregated atomics, so the order within a class
+// is arbitrary: tiles are independent and the order changes no output).
+// ctl: [0, 33) class counts, [33, 66) class bases, [66] blocks done; zero at launch.
+__global__ void __launch_bounds__(256) order_count_kernel(const uint2* __restrict__ ranges, uint32_t tiles,
+                                                          uint32_t* __restrict__ ctl) {
+    pdl_begin();
+    __shared__ uint32_t cnt[33];
+    __shared__ bool s_last;
+    if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
+        const uint2 r = ranges[t];
+        const uint32_t n = r.y - r.x;
+        atomicAdd(&cnt[n ? __clz(n) : 32], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 33 && cnt[threadIdx.x]) atomicAdd(&ctl[threadIdx.x], cnt[threadIdx.x]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&ctl[66], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        uint32_t run = 0;
+        for (int k = 0; k < 33; ++k) {
+            ctl[33 + k] = run;
+            run += __ldcg(&ctl[k]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) order_place_kernel(const uint2* __restrict__ ranges, uint32_t tiles,
+                                                          uint32_t* __restrict__ ctl, uint32_t* __restrict__ order) {
+    pdl_begin();
+    const uint32_t lane = threadIdx.x & 31u;
+    for (uint32_t t0 = blockIdx.x * blockDim.x; t0 < tiles; t0 += gridDim.x * blockDim.x) {
+        const uint32_t t = t0 + threadIdx.x;
+        uint32_t cls = 64u;
+        if (t < tiles) {
+            const uint2 r = ranges[t];
+            const uint32_t n = r.y - r.x;
+            cls = n ? __clz(n) : 32u;
+        }
+        const uint32_t peers = __match_any_sync(0xffffffffu, cls);
+        const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
+        uint32_t b = 0;
+        if (t < tiles && lane == leader) b = atomicAdd(&ctl[33 + cls], (uint32_t)__popc(peers));
         b = __shfl_sync(0xffffffffu, b, leader);
         if (t < tiles) order[b + (uint32_t)__popc(peers & ((1u << lane) - 1u))] = t;
     }
@@ -355,6 +413,14 @@ gs_status launch_ranges(gs_context* ctx, const FrameView& v) {
         (void)launch_pdl(ctx->stream, tile_order_kernel, dim3(1), dim3(1024), 0, v.ranges, (uint32_t)tiles,
                          v.tile_order);
         ctx->launches += 1;
+    } else if (tiles > 0 && v.order_ctl && (int64_t)tiles <= v.tile_order_cap) {
+        (void)launch_pdl(ctx->stream, zero_words_kernel, dim3(1), dim3(256), 0, v.order_ctl, (int64_t)67);
+        const unsigned blocks = (unsigned)std::min<size_t>((tiles + 255) / 256, (size_t)ctx->num_sms * 4);
+        (void)launch_pdl(ctx->stream, order_count_kernel, dim3(blocks), dim3(256), 0, v.ranges, (uint32_t)tiles,
+                         v.order_ctl);
+        (void)launch_pdl(ctx->stream, order_place_kernel, dim3(blocks), dim3(256), 0, v.ranges, (uint32_t)tiles,
+                         v.order_ctl, v.tile_order);
+        ctx->launches += 3;
     }
     return check_launch(ctx, "tile_ranges");
 }
@@ -382,7 +448,9 @@ gs_status launch_render(gs_context* ctx, const gs_raster_cfg* cfg, const FrameVi
     A.pixel_capacity = v.pixel_capacity;
     const unsigned tiles = (unsigned)(v.gx * v.gy);
     if (tiles == 0) return GS_OK;
-    A.order = tiles <= kMaxOrderedTiles ? v.tile_order : nullptr;  // written by launch_ranges
+    // written by launch_ranges
+    A.order = (tiles <= kMaxOrderedTiles || (v.order_ctl && (int64_t)tiles <= v.tile_order_cap)) ? v.tile_order
+                                                                                                   : nullptr;
     A.tiles = tiles;
 #define GS_BLEND_LAUNCH(T_, S_, M_) \
     (void)launch_pdl(ctx->stream, blend_kernel<T_, S_, M_>, dim3(tiles), dim3(T_ * T_), 0, A)

@@ -154,7 +154,7 @@ def test_autotuner_picks_and_caches(raster, tmp_path):
     ds = scene.to("cuda:0")
     path = tmp_path / "cache.json"
     a = autotune.tune(ds, cams, "cuda:0", reps=2, cache_path=path)
-    assert a["tile"] in (8, 16, 32) and not a["cached"] and len(a["timings"]) == 6
+    assert a["tile"] in (8, 16, 32) and not a["cached"] and len(a["timings"]) == 15
     b = autotune.tune(ds, cams, "cuda:0", reps=2, cache_path=path)
     assert b["cached"] and b["tile"] == a["tile"]
     # the choice changes speed only: AccuTile images agree across tile edges
@@ -165,3 +165,26 @@ def test_autotuner_picks_and_caches(raster, tmp_path):
         ims.append([im.cpu().numpy().copy() for im in imgs])
     for c in range(len(cams)):
         assert np.array_equal(ims[0][c], ims[1][c]) and np.array_equal(ims[1][c], ims[2][c])
+
+
+def test_batch_over_32768_tiles_equals_single_view(raster):
+    """A batch of 162,000 tiles (5 cameras at 1920x1080, tile 8): its tiles
+    launch heaviest first in the multi-block order; every camera's image and
+    keys equal its single-view render."""
+    scene = synth.blob_scene(20000, seed=78, n_blobs=20)
+    gen = torch.Generator().manual_seed(79)
+    cams = [synth.orbit_camera(gen, 1920, 1080) for _ in range(5)]
+    ds = scene.to("cuda:0")
+    br = raster.BatchRenderer("cuda:0", tile=8)
+    imgs, K = br.render(ds, cams)
+    assert br.frame.tile_capacity > 32768
+    imgs = [im.cpu().numpy().copy() for im in imgs]
+    keys = br.frame.keys[:K].cpu().numpy().view(np.uint64)
+    toff, _, _, _ = raster.batch_layout(cams, 8)
+    tiles = (keys >> np.uint64(32)).astype(np.int64)
+    for c, cam in enumerate(cams):
+        img1, k1, v1 = single_view(raster, ds, cam, 2, 8)
+        assert np.array_equal(imgs[c], img1), c
+        gx, gy = (cam.width + 7) // 8, (cam.height + 7) // 8
+        sel = (tiles >= toff[c]) & (tiles < toff[c] + gx * gy)
+        assert int(sel.sum()) == len(k1)
