@@ -493,7 +493,7 @@ def run_ours(args):
     K = keys["accutile"]
     hw = cam.width * cam.height
     tiles = f_acc.gx * f_acc.gy
-    passes = raster_sort_passes(cam.width, cam.height, args.tile)
+    passes, digit_bits, depth_bits = rast.gs_read_sort_plan(cfg_acc, f_acc)
     st = stages["accutile"] if stages else T.stages("accutile", 3)
     work = stage_work(st, n, n_counted, K, 4 * 3 * (scene.sh_degree + 1) ** 2, hw, tiles, passes)
     hbm = pk["hbm_gbs"]
@@ -502,6 +502,8 @@ def run_ours(args):
         gbs = work[k] / (st[k] * 1e-3) / 1e9
         stage_frac[k] = {"ms": st[k], "algorithmic_bytes": work[k], "gbs": gbs, "hbm_frac": gbs / hbm}
     stage_frac["sort"]["design_bytes"] = work["sort_design"]
+    stage_frac["sort"]["plan"] = {"passes": passes, "digit_bits": digit_bits, "depth_bits_kept": depth_bits,
+                                  "tile_bits": max(tiles - 1, 0).bit_length()}
     stage_frac["sort"]["design_hbm_frac"] = work["sort_design"] / (st["sort"] * 1e-3) / 1e9 / hbm
     # blend work per evaluated pair (dx, dy, 2b dy, c dy dy, two fma, compare):
     # 8 flop; per contributing pair about 10 more (alpha, T (1 - alpha), stop
@@ -839,15 +841,6 @@ def run_serving(args, dev, scene_3m):
         out["rates"][str(int(rate))] = {k: st[k] for k in ("requests", "p50_ms", "p99_ms", "frames_per_s",
                                                             "mean_batch", "max_inflight_batches", "span_s")}
     return out
-
-
-def raster_sort_passes(width, height, tile):
-    tiles = ((width + tile - 1) // tile) * ((height + tile - 1) // tile)
-    b = 0
-    while (1 << b) < tiles:
-        b += 1
-    bits = 32 + b
-    return 2 * ((bits + 15) // 16)
 
 
 def main():

@@ -57,6 +57,7 @@ typedef enum gs_mode {
 #define GS_FLAG_CAPACITY 1u   /* keys did not fit: nothing was emitted            */
 #define GS_FLAG_TIMEOUT  2u   /* a sort look-back wait exceeded its bound         */
 #define GS_FLAG_BATCH    4u   /* batch cameras exceed the frame's tile or pixel capacity */
+#define GS_FLAG_KEYRANGE 8u   /* gs_sort met a key outside the range gs_intersect recorded */
 
 /* Gaussian parameter set G_i = {mu, s, r, h, sigma} (Sec. 3.1), planar
  * structure of arrays, float32, device memory, read only.
@@ -179,9 +180,20 @@ gs_status gs_preprocess(gs_context* ctx, const gs_scene* scene, const gs_camera*
 gs_status gs_intersect(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame,
                        int64_t* num_keys);
 
-/* RadixSort (Sec. 3.2.2): stable LSD radix sort of the K pairs by key, over
- * the 32 depth bits plus ceil(log2(tiles)) tile bits, in an even number of
- * onesweep passes, result in keys[0]/vals[0].  Uses frame->scratch. */
+/* RadixSort (Sec. 3.2.2): stable LSD radix sort of the K pairs by key, in
+ * onesweep passes, result in keys[0]/vals[0].  Uses frame->scratch and
+ * keys[1]/vals[1].  The passes cover ceil(log2(tiles)) tile bits plus only
+ * as many depth bits as the frame's depths span: gs_preprocess records the
+ * least and greatest depth bits of the Gaussians it gave tiles, and the sort
+ * orders each key by (tile, depth bits - least), an order-preserving map of
+ * the K keys, so the result is the sort by the full key.  The pass count is
+ * therefore chosen on the device (the launches beyond it return at once);
+ * here it is even, so that passes alternating between the two buffers end in
+ * keys[0] (gs_forward, which also runs the emit, allows an odd count by
+ * having the emit write keys[1]).  The keys sorted must be the ones
+ * gs_intersect emitted after the frame's gs_preprocess: a key outside the
+ * recorded range sets GS_FLAG_KEYRANGE, the later stages see no keys, and
+ * gs_read_status returns GS_ERR_INVALID. */
 gs_status gs_sort(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame);
 
 /* identifyTileRanges (Sec. 3.2.2): ranges[tile] = [start, end) of the tile's
@@ -211,7 +223,11 @@ gs_status gs_render(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* 
 gs_status gs_render_stats(gs_context* ctx, const gs_camera* cam, const gs_raster_cfg* cfg, const gs_frame* frame,
                           uint64_t* evaluated, uint64_t* contributed, uint64_t* executed);
 
-/* The five stages above in one call, with no host synchronisation. */
+/* The five stages above in one call, with no host synchronisation.  The
+ * results equal the stage-by-stage calls'; the one difference is where the
+ * emitted pairs wait for the sort: when the sort plan has an odd number of
+ * passes the emit writes keys[1]/vals[1], so the sort needs no extra pass
+ * to end in keys[0]/vals[0]. */
 gs_status gs_forward(gs_context* ctx, const gs_scene* scene, const gs_camera* cam, const gs_raster_cfg* cfg,
                      const gs_frame* frame);
 
@@ -286,7 +302,7 @@ gs_status gs_pup_score(gs_context* ctx, const float* hessian, int64_t n, float* 
  *     The frame's own status words are not written, so the later stages
  *     (gs_sort ...) need gs_intersect.
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress).
  *   - Allocates nothing; all calls on a device share the array and it keeps
  *     the last call's contents (the call clears what must start at zero), so
  *     calls whose GPU work overlaps (other streams or host threads) race. */
@@ -364,6 +380,15 @@ gs_status gs_read_status(gs_context* ctx, const gs_frame* frame, int64_t* num_ke
  * valid only if the buffer was zero-filled once (the library keeps the word
  * consistent afterwards). */
 gs_status gs_read_culled(gs_context* ctx, const gs_frame* frame, int64_t* culled);
+
+/* The sort plan for the keys gs_intersect last emitted into the frame, with
+ * cfg's sort_digit_bits: the number of onesweep passes gs_forward runs (a
+ * stand-alone gs_sort runs the next even number), the bits per digit at that
+ * count, and how many depth bits the keys keep (their depths' span; 32 when
+ * nothing was recorded).  All three outputs are host pointers and nullable.
+ * Synchronises the stream. */
+gs_status gs_read_sort_plan(gs_context* ctx, const gs_raster_cfg* cfg, const gs_frame* frame, int32_t* passes,
+                            int32_t* digit_bits, int32_t* depth_bits);
 
 /* Failure detection of the sort's bounded waits.  Each decoupled look-back
  * wait of gs_sort gives up after max_polls polls (0 = the default, 4,194,304,

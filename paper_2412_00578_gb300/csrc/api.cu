@@ -33,7 +33,7 @@ constexpr int64_t kAlign = 256;
 int64_t align_up(int64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 }  // namespace
 
-ScratchLayout scratch_layout(int64_t ncap, int64_t kcap) {
+ScratchLayout scratch_layout(int64_t ncap, int64_t kcap, int64_t range_warps) {
     ScratchLayout L;
     int64_t off = 0;
     L.status = off;
@@ -46,6 +46,12 @@ ScratchLayout scratch_layout(int64_t ncap, int64_t kcap) {
     off += align_up(2 * std::max<int64_t>(sort_partitions_for(kcap), 1) * 256 * 4);
     L.order = off;
     off += align_up((int64_t)kMaxOrderedTiles * 4);
+    L.warp_range = off;
+    off += align_up(std::max<int64_t>(range_warps ? range_warps : (ncap + kPreThreads - 1) / kPreThreads *
+                                                                     (kPreThreads / 32),
+                                      1) * 8);
+    L.block_range = off;
+    off += align_up(std::max<int64_t>(scan_blocks_for(ncap), 1) * 8);
     L.total = off;
     return L;
 }
@@ -116,9 +122,7 @@ bool make_view(gs_context* ctx, const gs_frame* f, FrameView* v, unsigned need) 
     v->p2 = proj + 2 * f->n_capacity;
     v->counts = f->counts;
     v->keys0 = f->keys;
-    v->keys1 = f->keys + f->key_capacity;
     v->vals0 = f->vals;
-    v->vals1 = f->vals + f->key_capacity;
     v->ranges = reinterpret_cast<uint2*>(f->ranges);
     v->image = f->image;
     v->final_T = f->final_T;
@@ -133,6 +137,8 @@ bool make_view(gs_context* ctx, const gs_frame* f, FrameView* v, unsigned need) 
     v->sort_partitions = std::max<int64_t>(sort_partitions_for(f->key_capacity), 1);
     v->tile_order = reinterpret_cast<uint32_t*>(s + L.order);
     v->tile_order_cap = kMaxOrderedTiles;
+    v->warp_range = reinterpret_cast<uint2*>(s + L.warp_range);
+    v->block_range = reinterpret_cast<uint2*>(s + L.block_range);
     if ((reinterpret_cast<uintptr_t>(f->proj) & 15) || (reinterpret_cast<uintptr_t>(f->keys) & 7) ||
         (reinterpret_cast<uintptr_t>(f->ranges) & 7) || (reinterpret_cast<uintptr_t>(f->scratch) & 15)) {
         set_error(ctx, GS_ERR_INVALID, "frame buffer misaligned (proj/scratch need 16 B, keys/ranges 8 B)");
@@ -285,8 +291,8 @@ gs_status gs_forward(gs_context* ctx, const gs_scene* scene, const gs_camera* ca
     if ((st = check_cam(ctx, cam, frame)) || (st = check_cfg(ctx, cfg, frame))) return st;
     if ((st = check_scene(ctx, scene, frame))) return st;
     if ((st = launch_preprocess(ctx, scene, cam, cfg, v))) return st;
-    if ((st = launch_intersect(ctx, cfg, v))) return st;
-    if ((st = launch_sort(ctx, v, cfg->sort_digit_bits))) return st;
+    if ((st = launch_intersect(ctx, cfg, v, true))) return st;
+    if ((st = launch_sort(ctx, v, cfg->sort_digit_bits, true))) return st;
     if ((st = launch_ranges(ctx, v))) return st;
     return launch_render(ctx, cfg, v);
 }
@@ -357,6 +363,25 @@ gs_status gs_read_culled(gs_context* ctx, const gs_frame* frame, int64_t* culled
     return GS_OK;
 }
 
+gs_status gs_read_sort_plan(gs_context* ctx, const gs_raster_cfg* cfg, const gs_frame* frame, int32_t* passes,
+                            int32_t* digit_bits, int32_t* depth_bits) {
+    gs_status st = enter(ctx);
+    if (st) return st;
+    FrameView v;
+    if (!make_view(ctx, frame, &v, kNeedEmit)) return GS_ERR_INVALID;
+    if ((st = check_cfg(ctx, cfg, frame))) return st;
+    uint32_t w[kStatusWords] = {0};
+    cudaError_t e = cudaMemcpyAsync(w, v.status, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return set_error(ctx, GS_ERR_CUDA, "read_sort_plan: %s", cudaGetErrorString(e));
+    const SortPlan P = sort_plan_of(w[kStatusDepthLoN], w[kStatusDepthHi], sort_tile_bits((int64_t)v.gx * v.gy),
+                                    sort_digit_max(cfg->sort_digit_bits), true);
+    if (passes) *passes = P.passes;
+    if (digit_bits) *digit_bits = P.dbits;
+    if (depth_bits) *depth_bits = P.w;
+    return GS_OK;
+}
+
 gs_status gs_read_status(gs_context* ctx, const gs_frame* frame, int64_t* num_keys, uint32_t* flags) {
     gs_status st = enter(ctx);
     if (st) return st;
@@ -373,6 +398,8 @@ gs_status gs_read_status(gs_context* ctx, const gs_frame* frame, int64_t* num_ke
         return set_error(ctx, GS_ERR_CAPACITY, "%lld keys exceed key_capacity %lld", (long long)K,
                          (long long)frame->key_capacity);
     if (w[2] & GS_FLAG_TIMEOUT) return set_error(ctx, GS_ERR_TIMEOUT, "sort look-back wait exceeded its bound");
+    if (w[2] & GS_FLAG_KEYRANGE)
+        return set_error(ctx, GS_ERR_INVALID, "gs_sort met a key outside the range gs_intersect recorded");
     return GS_OK;
 }
 

@@ -20,7 +20,9 @@ struct BatchLayout {
 // batch's tiles and the counters of the multi-block ordering.
 BatchLayout batch_layout(int64_t n_capacity, int64_t max_cams, int64_t kcap, int64_t tile_capacity) {
     BatchLayout L;
-    L.base = scratch_layout(n_capacity * max_cams, kcap);
+    // the multi-view preprocess runs ceil(n / 256) blocks per camera
+    L.base = scratch_layout(n_capacity * max_cams, kcap,
+                            (n_capacity + kPreThreads - 1) / kPreThreads * (kPreThreads / 32) * max_cams);
     L.table = L.base.total;
     L.order = L.table + align_up(max_cams * (int64_t)sizeof(CamRec));
     L.ctl = L.order + align_up(tile_capacity * 4);
@@ -113,9 +115,7 @@ bool make_batch_view(gs_context* ctx, const gs_batch_frame* f, int num_cams, Fra
     v->p2 = proj + 2 * stride;
     v->counts = f->counts;
     v->keys0 = f->keys;
-    v->keys1 = f->keys + f->key_capacity;
     v->vals0 = f->vals;
-    v->vals1 = f->vals + f->key_capacity;
     v->ranges = reinterpret_cast<uint2*>(f->ranges);
     v->image = f->image;
     v->final_T = f->final_T;
@@ -130,6 +130,8 @@ bool make_batch_view(gs_context* ctx, const gs_batch_frame* f, int num_cams, Fra
     v->sort_partitions = std::max<int64_t>(sort_partitions_for(f->key_capacity), 1);
     v->tile_order = reinterpret_cast<uint32_t*>(s + L.order);
     v->tile_order_cap = f->tile_capacity;
+    v->warp_range = reinterpret_cast<uint2*>(s + L.base.warp_range);
+    v->block_range = reinterpret_cast<uint2*>(s + L.base.block_range);
     v->order_ctl = reinterpret_cast<uint32_t*>(s + L.ctl);
     v->table = reinterpret_cast<const CamRec*>(s + L.table);
     v->num_cams = num_cams;
@@ -193,8 +195,8 @@ gs_status gs_forward_batch(gs_context* ctx, const gs_scene* scene, const gs_came
     gs_status st = check_launch(ctx, "batch_setup");
     if (st) return st;
     if ((st = launch_preprocess(ctx, scene, nullptr, cfg, v))) return st;
-    if ((st = launch_intersect(ctx, cfg, v))) return st;
-    if ((st = launch_sort(ctx, v, cfg->sort_digit_bits))) return st;
+    if ((st = launch_intersect(ctx, cfg, v, true))) return st;
+    if ((st = launch_sort(ctx, v, cfg->sort_digit_bits, true))) return st;
     if ((st = launch_ranges(ctx, v))) return st;
     return launch_render(ctx, cfg, v);
 }
@@ -219,6 +221,8 @@ gs_status gs_batch_status(gs_context* ctx, const gs_batch_frame* frame, int64_t*
         return set_error(ctx, GS_ERR_CAPACITY, "%lld keys exceed key_capacity %lld", (long long)K,
                          (long long)frame->key_capacity);
     if (fl & GS_FLAG_TIMEOUT) return set_error(ctx, GS_ERR_TIMEOUT, "sort look-back wait exceeded its bound");
+    if (fl & GS_FLAG_KEYRANGE)
+        return set_error(ctx, GS_ERR_INVALID, "gs_sort met a key outside the range gs_intersect recorded");
     return GS_OK;
 }
 

@@ -29,9 +29,15 @@ constexpr int kMaxTile = 32;
 //        parameters or a zero quaternion (accumulated, then moved to [11] and
 //        cleared by the scan that follows it)
 //   [11] that count for the last preprocessed frame
+//   [12] complement of the least and [13] greatest depth bits of the
+//        Gaussians the last preprocess gave tiles (written by the scan from
+//        the preprocess's per-warp ranges; both 0 when none was recorded);
+//        the sort plan follows from them (sort_plan_of)
 constexpr int kStatusWords = 16;
 constexpr int kStatusCulledAcc = 10;
 constexpr int kStatusCulled = 11;
+constexpr int kStatusDepthLoN = 12;
+constexpr int kStatusDepthHi = 13;
 // Bound of one sort look-back wait, in polls (about 32 ns apart).
 constexpr uint32_t kDefaultSpinLimit = 1u << 22;
 
@@ -59,16 +65,19 @@ struct FrameView {
     float4* p1;  // a, b, c, t
     float4* p2;  // r, g, b, radius bits
     int32_t* counts;
-    uint64_t* keys0;
-    uint64_t* keys1;
-    uint32_t* vals0;
-    uint32_t* vals1;
+    uint64_t* keys0;  // buffer 0; the sort's buffer 1 follows at keys0 + kcap
+    uint32_t* vals0;  // alike
     uint2* ranges;
     float* image;
     float* final_T;
     uint32_t* last;
     uint32_t* status;
     long long* scan_partials;  // one per scan block + 1
+    // depth-bit ranges (complement of the least, greatest) of the Gaussians
+    // given tiles: one per preprocess warp, then one per scan block; both
+    // nullptr where the frame has no scratch (the range is then not recorded)
+    uint2* warp_range = nullptr;
+    uint2* block_range = nullptr;
     uint32_t* sort_hist;       // [kMaxPasses][256]
     uint32_t* sort_ticket;     // [kMaxPasses]
     uint32_t* sort_lookback;   // [2][sort_partitions][256] look-back words, see sort.cu
@@ -275,22 +284,72 @@ constexpr unsigned kNeedAll = 0xffu;
 constexpr unsigned kNeedEmit = 1u;  // proj, counts, keys, vals only
 bool make_view(gs_context* ctx, const gs_frame* f, FrameView* v, unsigned need = kNeedAll);
 int sort_tile_bits(int64_t tiles);
-void sort_plan(int64_t tiles, int digit_override, int* passes, int* digit_bits);
+
+// A frame's sort plan (see sort.cu): pass count, bits per digit, depth bits
+// kept and the least depth bits, from status words [14] and [15].  At most
+// dmax bits per digit, at least two passes and at most kMaxPasses, an even
+// count unless `fused` (a chain that also runs the emit may start the passes
+// from either buffer); without a recorded range (both words zero) the whole
+// depth word is kept.
+struct SortPlan {
+    int passes, dbits, w;
+    uint32_t dmin;
+    int start;  // buffer the emit writes and the first pass reads
+};
+__host__ __device__ inline SortPlan sort_plan_of(uint32_t lo_n, uint32_t hi, int tile_bits, int dmax, bool fused) {
+    SortPlan P;
+    if ((lo_n | hi) == 0u) {
+        P.dmin = 0u;
+        P.w = 32;
+    } else {
+        P.dmin = ~lo_n;
+        uint32_t span = hi - P.dmin;
+        P.w = 0;
+        while (span) {
+            ++P.w;
+            span >>= 1;
+        }
+    }
+    const int total = tile_bits + P.w;
+    int p = (total + dmax - 1) / dmax;
+    p = p < 2 ? 2 : (p > kMaxPasses ? kMaxPasses : p);
+    if (!fused) p += p & 1;
+    P.passes = p;
+    P.dbits = (total + P.passes - 1) / P.passes;
+    P.start = P.passes & 1;  // so that the last pass writes buffer 0
+    return P;
+}
+// The most passes any plan of a frame with these tiles can need.
+inline int sort_max_passes(int tile_bits, int dmax, bool fused) {
+    int p = (32 + tile_bits + dmax - 1) / dmax;
+    p = p < 2 ? 2 : (p > kMaxPasses ? kMaxPasses : p);
+    if (!fused) p += p & 1;
+    return p;
+}
+// Bits per digit at most: the override when it is 4..8, else 8.
+inline int sort_digit_max(int digit_override) {
+    return (digit_override >= 4 && digit_override <= 8) ? digit_override : 8;
+}
 
 struct ScratchLayout {
-    int64_t status, partials, hist, lookback, order, total;
+    int64_t status, partials, hist, lookback, order, warp_range, block_range, total;
 };
 // Frames with more tiles than this blend them in index order.
 constexpr unsigned kMaxOrderedTiles = 1u << 15;
-ScratchLayout scratch_layout(int64_t ncap, int64_t kcap);
+// range_warps: preprocess warps of the largest launch (0: one per 32 slots)
+ScratchLayout scratch_layout(int64_t ncap, int64_t kcap, int64_t range_warps = 0);
+constexpr int kPreThreads = 256;  // preprocess block size
 int64_t sort_partitions_for(int64_t kcap);
 int64_t scan_blocks_for(int64_t n);
 
 // launchers (one per translation unit); all enqueue on ctx->stream
 gs_status launch_preprocess(gs_context* ctx, const gs_scene* s, const gs_camera* cam, const gs_raster_cfg* cfg,
                             const FrameView& v);
-gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v);
-gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override = 0);
+// fused: the call runs intersect and sort back to back (gs_forward,
+// gs_forward_batch), so the emit may write the buffer the sort plan starts
+// from; otherwise the emitted pairs are in buffer 0 and the plan is even.
+gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v, bool fused = false);
+gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override = 0, bool fused = false);
 // identifyTileRanges, then the blend's heaviest-first tile launch order
 // (for frames of at most kMaxOrderedTiles tiles).
 gs_status launch_ranges(gs_context* ctx, const FrameView& v);

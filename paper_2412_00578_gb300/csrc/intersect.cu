@@ -9,16 +9,51 @@
 //                memory round by round (so per-Gaussian offsets are never
 //                stored in HBM), and every Gaussian with tiles recomputes its tile set with
 //                the same localization function the count used and writes
-//                its (tile << 32 | depth bits, index) pairs at its offset.
+//                its (tile << 32 | depth bits, index) pairs at its offset,
+//                in buffer 0, or (for a fused forward call) in the buffer
+//                the sort plan starts from (scan_top's offsets say which).
 #include "tiles.cuh"
 
 namespace gs {
 namespace {
 
+// Maximum of both words of a uint2 over the block (result in thread 0).
+__device__ __forceinline__ uint2 block_max2(uint2 v, uint2* s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v.x = __reduce_max_sync(0xffffffffu, v.x);
+    v.y = __reduce_max_sync(0xffffffffu, v.y);
+    if (lane == 0) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        const bool w = lane < (int)(blockDim.x >> 5);
+        v.x = __reduce_max_sync(0xffffffffu, w ? s_warp[lane].x : 0u);
+        v.y = __reduce_max_sync(0xffffffffu, w ? s_warp[lane].y : 0u);
+    }
+    return v;
+}
+
+// Each block sums its kScanBlock counts and reduces its share of the
+// preprocess's per-warp depth ranges (an even split of the n_warps slots
+// over the blocks, independent of which Gaussians a warp held); one barrier
+// serves both reductions.
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const int32_t* __restrict__ counts, int64_t n,
-                                                                   long long* __restrict__ partials) {
+                                                                   long long* __restrict__ partials,
+                                                                   const uint2* __restrict__ warp_range,
+                                                                   int64_t n_warps, uint2* __restrict__ block_range) {
     pdl_begin();
-    __shared__ long long s_warp[32];
+    constexpr int kWarps = kScanThreads / 32;
+    __shared__ long long s_sum[kWarps];
+    __shared__ uint2 s_range[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint2 r = make_uint2(0u, 0u);
+    if (warp_range) {
+        const int64_t w0 = n_warps * blockIdx.x / gridDim.x, w1 = n_warps * (blockIdx.x + 1) / gridDim.x;
+        for (int64_t w = w0 + threadIdx.x; w < w1; w += kScanThreads) {
+            const uint2 x = warp_range[w];
+            r.x = max(r.x, x.x);
+            r.y = max(r.y, x.y);
+        }
+    }
     const int64_t base = (int64_t)blockIdx.x * kScanBlock;
     long long sum = 0;
 #pragma unroll 4
@@ -26,17 +61,70 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(const int32_t
         const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
         if (i < n) sum += counts[i];
     }
-    long long total;
-    block_excl_scan(sum, s_warp, &total);
-    if (threadIdx.x == 0) partials[blockIdx.x] = total;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    r.x = __reduce_max_sync(0xffffffffu, r.x);
+    r.y = __reduce_max_sync(0xffffffffu, r.y);
+    if (lane == 0) {
+        s_sum[warp] = sum;
+        s_range[warp] = r;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        long long t = lane < kWarps ? s_sum[lane] : 0;
+        uint2 m = lane < kWarps ? s_range[lane] : make_uint2(0u, 0u);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        m.x = __reduce_max_sync(0xffffffffu, m.x);
+        m.y = __reduce_max_sync(0xffffffffu, m.y);
+        if (lane == 0) {
+            partials[blockIdx.x] = t;
+            if (warp_range) block_range[blockIdx.x] = m;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(1024) scan_top_kernel(long long* __restrict__ partials, int64_t nblocks,
-                                                        int64_t kcap, uint32_t* __restrict__ status, bool clear3) {
+                                                        int64_t kcap, uint32_t* __restrict__ status, bool clear3,
+                                                        const uint2* __restrict__ block_range, bool fused,
+                                                        int tile_bits, int dmax, uint32_t* __restrict__ sort_ctl) {
     pdl_begin();
+    // a fused chain's sort control words (histograms, tickets) start at zero
+    if (sort_ctl)
+        for (int i = threadIdx.x; i < kSortCtlWords; i += blockDim.x) sort_ctl[i] = 0u;
     __shared__ long long s_warp[32];
+    __shared__ uint2 s_range[32];
     __shared__ long long s_carry;
-    if (threadIdx.x == 0) s_carry = 0;
+    __shared__ long long s_base;
+    // the frame's depth-bit range, from the scan blocks' shares
+    uint2 r = make_uint2(0u, 0u);
+    if (block_range) {
+        // four loads in flight per thread
+        for (int64_t b0 = threadIdx.x; b0 < nblocks; b0 += 4 * (int64_t)blockDim.x) {
+            uint2 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t b = b0 + (int64_t)u * blockDim.x;
+                x[u] = b < nblocks ? block_range[b] : make_uint2(0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                r.x = max(r.x, x[u].x);
+                r.y = max(r.y, x[u].y);
+            }
+        }
+    }
+    r = block_max2(r, s_range);
+    if (threadIdx.x == 0) {
+        s_carry = 0;
+        status[kStatusDepthLoN] = r.x;
+        status[kStatusDepthHi] = r.y;
+        // A fused call whose sort plan starts from buffer 1 has the emit write
+        // there: buffer 1 is buffer 0 displaced by the key capacity (keys and
+        // values alike), so every block offset starts at kcap.
+        const SortPlan P = sort_plan_of(r.x, r.y, tile_bits, dmax, true);
+        s_base = (fused && P.start) ? (long long)kcap : 0ll;
+    }
     __syncthreads();
     for (int64_t b0 = 0; b0 < nblocks; b0 += blockDim.x) {
         const int64_t b = b0 + threadIdx.x;
@@ -53,7 +141,7 @@ __global__ void __launch_bounds__(1024) scan_top_kernel(long long* __restrict__ 
         __syncthreads();
         const long long excl = (warp > 0 ? s_warp[warp - 1] : 0) + inc - v;
         const long long carry = s_carry;
-        if (b < nblocks) partials[b] = carry + excl;
+        if (b < nblocks) partials[b] = s_base + carry + excl;
         __syncthreads();
         if (threadIdx.x == 0) s_carry = carry + s_warp[31];
         __syncthreads();
@@ -82,7 +170,7 @@ struct EmitArgs {
     const float4* p1;
     const float4* p2;
     const uint32_t* status;
-    uint64_t* keys;
+    uint64_t* keys;  // buffer 0; buffer 1 follows at keys + kcap (vals alike)
     uint32_t* vals;
     int64_t n;
     int mode;
@@ -209,15 +297,20 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
 
 }  // namespace
 
-gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v) {
+gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const FrameView& v, bool fused) {
     const int64_t nb = scan_blocks_for(v.ncap);
+    // preprocess warps that stored a depth range: ceil(n / 256) blocks (per camera)
+    const int64_t per_cam = v.table ? v.cam_stride : v.ncap;
+    const int64_t n_warps = (per_cam + kPreThreads - 1) / kPreThreads * (kPreThreads / 32) * (v.table ? v.num_cams : 1);
     if (nb > 0) {
         (void)launch_pdl(ctx->stream, scan_reduce_kernel, dim3((unsigned)nb), dim3(kScanThreads), 0, v.counts, v.ncap,
-                         v.scan_partials);
+                         v.scan_partials, (const uint2*)v.warp_range, n_warps, v.block_range);
         ctx->launches += 1;
     }
     (void)launch_pdl(ctx->stream, scan_top_kernel, dim3(1), dim3(1024), 0, v.scan_partials, nb, v.kcap, v.status,
-                     v.table == nullptr);
+                     v.table == nullptr, (const uint2*)(v.warp_range ? v.block_range : nullptr), fused,
+                     sort_tile_bits((int64_t)v.gx * v.gy), sort_digit_max(cfg->sort_digit_bits),
+                     fused ? v.sort_hist : nullptr);
     ctx->launches += 1;
     if (nb > 0) {
         EmitArgs A;

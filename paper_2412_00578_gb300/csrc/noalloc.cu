@@ -91,6 +91,8 @@ extern "C" gs_status gs_intersect_noalloc(gs_context* ctx, const gs_camera* cam,
     if (reinterpret_cast<const unsigned char*>(v.status) != static_cast<unsigned char*>(scratch) ||
         end > static_cast<unsigned char*>(scratch) + kNoAllocBytes)
         return set_error(ctx, GS_ERR_INVALID, "intersect_noalloc: working-memory layout does not fit");
+    v.warp_range = nullptr;  // outside the fixed array: no depth range (this path does not sort)
+    v.block_range = nullptr;
     if ((st = launch_intersect(ctx, cfg, v))) return st;  // clears the status words first
     uint32_t w[3] = {0, 0, 0};
     cudaError_t e = cudaMemcpyAsync(w, v.status, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream);

@@ -31,6 +31,7 @@ struct PreArgs {
     const CamRec* table;  // multi-view: per-camera constants (else nullptr)
     int num_cams;
     uint32_t* culled;     // count of non-finite / zero-quaternion Gaussians (nullable)
+    uint2* warp_range;    // per warp: complement of the least, greatest depth bits
 };
 
 // Real SH normalisation constants, from their closed forms:
@@ -69,9 +70,12 @@ __device__ __forceinline__ void sh_basis16(float x, float y, float z, float Y[16
 }
 
 // Gaussian i seen by camera C (grid g); writes slot o of the outputs.
-__device__ __forceinline__ void preprocess_one(const PreArgs& A, const CamK& C, const Grid& grid, int64_t i,
-                                               int64_t o) {
+// Returns the depth bits of a Gaussian given tiles, else 0 (a counted
+// depth is above the near plane, so its bits are never 0).
+__device__ __forceinline__ uint32_t preprocess_one(const PreArgs& A, const CamK& C, const Grid& grid, int64_t i,
+                                                   int64_t o) {
     int count = 0;
+    uint32_t depth_bits = 0u;
     if (i < A.n) {
         const int64_t n = A.n;
         const float mx = __ldg(A.means + i), my = __ldg(A.means + n + i), mz = __ldg(A.means + 2 * n + i);
@@ -216,6 +220,7 @@ __device__ __forceinline__ void preprocess_one(const PreArgs& A, const CamK& C, 
                             rgb[ch] = acc < 0.0f ? 0.0f : acc;
                         }
                         A.p0[o] = make_float4(u, v, sigma, pz);
+                        depth_bits = __float_as_uint(pz);
                         A.p1[o] = make_float4(a, b, c, t);
                         A.p2[o] = make_float4(rgb[0], rgb[1], rgb[2], __int_as_float(radius));
                     }
@@ -224,24 +229,38 @@ __device__ __forceinline__ void preprocess_one(const PreArgs& A, const CamK& C, 
         }
     }
     A.counts[o] = count;
+    return depth_bits;
 }
 
-__global__ void __launch_bounds__(256, 4) preprocess_kernel(const PreArgs A) {
+// Least and greatest depth bits of the warp's Gaussians with tiles, stored
+// (as the complement of the least, and the greatest) in the warp's slot; the
+// scan reduces the slots and the sort keeps only the bits they span.
+__device__ __forceinline__ void record_depth_range(uint2* out, uint32_t db) {
+    const uint32_t lo_n = __reduce_max_sync(0xffffffffu, db ? ~db : 0u);
+    const uint32_t hi = __reduce_max_sync(0xffffffffu, db);
+    if ((threadIdx.x & 31) == 0 && out)
+        out[(int64_t)blockIdx.x * (kPreThreads / 32) + (threadIdx.x >> 5)] = make_uint2(lo_n, hi);
+}
+
+__global__ void __launch_bounds__(kPreThreads, 4) preprocess_kernel(const PreArgs A) {
     pdl_begin();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= A.ncap) return;
-    preprocess_one(A, A.cam, A.grid, i, i);
+    const uint32_t db = i < A.ncap ? preprocess_one(A, A.cam, A.grid, i, i) : 0u;
+    record_depth_range(A.warp_range, db);
 }
 
 // Multi-view: block b handles Gaussian chunk b / V for camera b % V, so the
 // cameras of one chunk run back to back and re-read its parameters from L2.
-__global__ void __launch_bounds__(256, 4) preprocess_multiview_kernel(const PreArgs A) {
+__global__ void __launch_bounds__(kPreThreads, 4) preprocess_multiview_kernel(const PreArgs A) {
     const int cam = (int)(blockIdx.x % (unsigned)A.num_cams);
     const int64_t i = (int64_t)(blockIdx.x / (unsigned)A.num_cams) * blockDim.x + threadIdx.x;
-    if (i >= A.ncap) return;
-    const CamRec& R = A.table[cam];
-    const Grid g{A.grid.T, R.gx, R.gy, R.width, R.height};
-    preprocess_one(A, R.k, g, i, (int64_t)cam * A.ncap + i);
+    uint32_t db = 0u;
+    if (i < A.ncap) {
+        const CamRec& R = A.table[cam];
+        const Grid g{A.grid.T, R.gx, R.gy, R.width, R.height};
+        db = preprocess_one(A, R.k, g, i, (int64_t)cam * A.ncap + i);
+    }
+    record_depth_range(A.warp_range, db);
 }
 
 }  // namespace
@@ -277,7 +296,8 @@ gs_status launch_preprocess(gs_context* ctx, const gs_scene* s, const gs_camera*
     A.table = v.table;
     A.num_cams = v.num_cams;
     A.culled = v.table ? nullptr : v.status + kStatusCulledAcc;
-    const int threads = 256;
+    A.warp_range = v.warp_range;
+    const int threads = kPreThreads;
     if (v.table) {
         A.ncap = v.cam_stride;
         if (A.ncap == 0 || v.num_cams == 0) return GS_OK;

@@ -27,20 +27,30 @@
 namespace gs {
 namespace {
 
-// Keys present in the buffer (see sort.cu): none when the emit was skipped
-// or a sort wait gave up.
+// Keys present in the buffer (see sort.cu): none when the emit was skipped,
+// a sort wait gave up or the sort met a key outside the recorded range.
 __device__ __forceinline__ uint32_t frame_keys_r(const uint32_t* status) {
-    return ((status[2] & (GS_FLAG_CAPACITY | GS_FLAG_TIMEOUT)) || status[3]) ? 0u : status[0];
+    return ((status[2] & (GS_FLAG_CAPACITY | GS_FLAG_TIMEOUT | GS_FLAG_KEYRANGE)) || status[3]) ? 0u : status[0];
 }
 
 // Four consecutive keys per thread (two 16-byte loads when the buffer is
 // 16-byte aligned) plus the key before them: a key whose tile differs from its
-// predecessor's closes the previous range and opens its own.
+// predecessor's closes the previous range and opens its own, and writes
+// [0, 0) for the empty tiles between the two.  The whole grid writes [0, 0)
+// for the tiles before the first key's and after the last key's (all tiles
+// when there are no keys).  Every word of the ranges is written exactly
+// once, so no zero-fill precedes the kernel.
 __global__ void __launch_bounds__(256) ranges_kernel(const uint64_t* __restrict__ keys,
-                                                     const uint32_t* __restrict__ status, uint2* __restrict__ ranges) {
+                                                     const uint32_t* __restrict__ status, uint2* __restrict__ ranges,
+                                                     uint32_t tiles) {
     pdl_begin();
     const uint32_t K = frame_keys_r(status);
-    const uint32_t i0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4u;
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    const uint32_t i0 = g * 4u;
+    const uint32_t t_first = K ? (uint32_t)(keys[0] >> 32) : tiles;
+    const uint32_t t_last = K ? (uint32_t)(keys[K - 1] >> 32) : tiles;
+    for (uint32_t t = g; t < t_first; t += stride) ranges[t] = make_uint2(0u, 0u);
+    for (uint32_t t = t_last + 1u + g; t < tiles; t += stride) ranges[t] = make_uint2(0u, 0u);
     if (i0 >= K) return;
     uint32_t t[4];
     // the frame only guarantees 8-byte alignment of keys: vector loads only
@@ -66,6 +76,7 @@ __global__ void __launch_bounds__(256) ranges_kernel(const uint64_t* __restrict_
         } else if (prev != t[j]) {
             ranges[prev].y = i;
             ranges[t[j]].x = i;
+            for (uint32_t e = prev + 1; e < t[j]; ++e) ranges[e] = make_uint2(0u, 0u);
         }
         if (i == K - 1) ranges[t[j]].y = K;
         prev = t[j];
@@ -399,13 +410,12 @@ __global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 4 : 16)) blend_
 
 gs_status launch_ranges(gs_context* ctx, const FrameView& v) {
     const size_t tiles = (size_t)v.gx * v.gy;
-    (void)launch_pdl(ctx->stream, zero_words_kernel, dim3(zero_blocks(2 * (int64_t)tiles)), dim3(256), 0,
-                     reinterpret_cast<uint32_t*>(v.ranges), 2 * (int64_t)tiles);
-    ctx->launches += 1;
-    if (v.kcap > 0) {
-        const int64_t blocks = (v.kcap + 1023) / 1024;  // 4 keys per thread
+    if (tiles > 0) {
+        // 4 keys per thread; at least enough threads to clear the tiles in a few strides
+        const int64_t blocks =
+            std::max<int64_t>((v.kcap + 1023) / 1024, std::min<int64_t>(((int64_t)tiles + 255) / 256, 1024));
         (void)launch_pdl(ctx->stream, ranges_kernel, dim3((unsigned)blocks), dim3(256), 0, v.keys0, v.status,
-                         v.ranges);
+                         v.ranges, (uint32_t)tiles);
         ctx->launches += 1;
     }
     // the blend's launch order, from the ranges just found

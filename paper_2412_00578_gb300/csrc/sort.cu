@@ -19,8 +19,20 @@
 //               reached the block records GS_FLAG_TIMEOUT and proceeds, so
 //               no kernel can hang.
 //
-// Bits sorted: the 32 depth bits plus ceil(log2(tiles)) tile bits, split
-// into an even number of passes so the result lands back in buffer 0.
+// Bits sorted: ceil(log2(tiles)) tile bits plus the w depth bits that the
+// frame's depths span.  The preprocess records the least (dmin) and greatest
+// depth bits of the Gaussians it gave tiles; every key is ordered by its
+// image (tile << w) | (depth bits - dmin), which is strictly increasing in
+// the key over the frame's keys, so sorting the images sorts the keys.  The
+// first pass turns each key it reads into its image, the passes in between
+// move images, and the last pass writes each key back in full.  The plan (pass count P, digit width) is a
+// function of the status words, evaluated alike by every block of every
+// sort kernel (sort_plan_of); the host launches the most passes any plan of
+// the frame can need and the launches past P return at once.  The passes
+// alternate between buffers 0 and 1 and the last one writes buffer 0: a
+// stand-alone gs_sort (whose keys gs_intersect left in buffer 0) rounds P up
+// to even, while gs_forward's chain lets the emit write buffer 1 when P is
+// odd (the scan's offsets say where).
 //
 // Finding the lanes with equal digits: warp match costs more the more
 // distinct digits a warp holds; a shared-memory atomicOr of each lane's bit
@@ -43,21 +55,40 @@ constexpr uint32_t kNoDigit = 0xffffffffu;
 constexpr int kLookWindow = 16;  // predecessors inspected per look-back step
 
 // Keys present in the buffer: none when the emit was skipped (keys over
-// capacity, or batch cameras over the frame's tile/pixel capacity), and none
+// capacity, or batch cameras over the frame's tile/pixel capacity), none
 // once a look-back wait has given up (the pass that gave up may have placed
-// keys wrongly, so no later pass, range or blend reads them).
+// keys wrongly, so no later pass, range or blend reads them), and none when
+// a key lies outside the recorded range.
 __device__ __forceinline__ uint32_t frame_keys(const uint32_t* status) {
-    return ((status[2] & (GS_FLAG_CAPACITY | GS_FLAG_TIMEOUT)) || status[3]) ? 0u : status[0];
+    return ((status[2] & (GS_FLAG_CAPACITY | GS_FLAG_TIMEOUT | GS_FLAG_KEYRANGE)) || status[3]) ? 0u : status[0];
+}
+
+using DevPlan = SortPlan;
+
+__device__ __forceinline__ DevPlan device_plan(const uint32_t* status, int tile_bits, int dmax, bool fused) {
+    return sort_plan_of(status[kStatusDepthLoN], status[kStatusDepthHi], tile_bits, dmax, fused);
+}
+
+// The key's image (tile << w) | (depth bits - dmin), whose digits the passes sort.
+__device__ __forceinline__ uint64_t plan_image(uint64_t k, const DevPlan& P) {
+    return ((k >> 32) << P.w) | (uint64_t)((uint32_t)k - P.dmin);
+}
+// The key of an image.
+__device__ __forceinline__ uint64_t plan_key(uint64_t im, const DevPlan& P) {
+    const uint32_t rel = P.w < 32 ? (uint32_t)im & ((1u << P.w) - 1u) : (uint32_t)im;
+    return ((im >> P.w) << 32) | (uint64_t)(rel + P.dmin);
 }
 
 struct HistArgs {
-    const uint64_t* keys;
-    const uint32_t* status;
+    const uint64_t* keys;  // buffer 0; buffer 1 follows at keys + kcap
+    int64_t kcap;
+    bool fused;
+    uint32_t* status;
     uint32_t* hist;        // [passes][256]
     uint32_t* lookback0;   // first pass's table, cleared here
     uint32_t* method;      // [passes]: 1 = rank by warp match, 0 = by atomicOr
     uint32_t* done;        // blocks finished (zero at launch)
-    int passes, dbits;
+    int tile_bits, dmax;
 };
 
 constexpr uint32_t kRankMatch = 1u;
@@ -65,31 +96,37 @@ constexpr uint32_t kRankMatch = 1u;
 __global__ void __launch_bounds__(256) sort_hist_kernel(const HistArgs A) {
     pdl_begin();
     __shared__ uint32_t sh[kMaxPasses * 256];
-    for (int i = threadIdx.x; i < A.passes * 256; i += blockDim.x) sh[i] = 0;
+    const DevPlan P = device_plan(A.status, A.tile_bits, A.dmax, A.fused);
+    const uint64_t* keys = A.keys + (P.start ? A.kcap : 0);
+    for (int i = threadIdx.x; i < P.passes * 256; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     const uint32_t K = frame_keys(A.status);
-    const uint32_t mask = (1u << A.dbits) - 1u;
+    const uint32_t mask = (1u << P.dbits) - 1u;
     const uint32_t stride = gridDim.x * blockDim.x;
+    // a key outside the recorded range (or past the tile bits) has no image
+    const uint32_t wmask = P.w < 32 ? ~((1u << P.w) - 1u) : 0u;
+    bool bad = false;
+    auto count = [&](uint64_t key) {
+        bad |= ((((uint32_t)key - P.dmin) & wmask) != 0u) || ((key >> 32) >> A.tile_bits) != 0ull;
+        const uint64_t im = plan_image(key, P);
+        for (int p = 0; p < P.passes; ++p) atomicAdd(&sh[p * 256 + (uint32_t)((im >> (p * P.dbits)) & mask)], 1u);
+    };
     // four keys per thread and step, all loaded before any is counted
     uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     for (; i + 3u * stride < K; i += 4u * stride) {
         uint64_t key[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) key[u] = A.keys[i + (uint32_t)u * stride];
+        for (int u = 0; u < 4; ++u) key[u] = keys[i + (uint32_t)u * stride];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            for (int p = 0; p < A.passes; ++p)
-                atomicAdd(&sh[p * 256 + (uint32_t)((key[u] >> (p * A.dbits)) & mask)], 1u);
+        for (int u = 0; u < 4; ++u) count(key[u]);
     }
-    for (; i < K; i += stride) {
-        const uint64_t key = A.keys[i];
-        for (int p = 0; p < A.passes; ++p) atomicAdd(&sh[p * 256 + (uint32_t)((key >> (p * A.dbits)) & mask)], 1u);
-    }
+    for (; i < K; i += stride) count(keys[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(A.status + 2, GS_FLAG_KEYRANGE);
     // clear the look-back words of the partitions the first pass will use
     const uint32_t words = ((K + kSortPartition - 1) / kSortPartition) * 256u;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) A.lookback0[i] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < A.passes * 256; i += blockDim.x)
+    for (int i = threadIdx.x; i < P.passes * 256; i += blockDim.x)
         if (sh[i]) atomicAdd(&A.hist[i], sh[i]);
     // The last block to finish sees every block's counts and sets the
     // passes' ranking methods (warp w handles passes w, w + 8, ...).
@@ -102,7 +139,7 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const HistArgs A) {
     __threadfence();
     const int lane = threadIdx.x & 31;
     const double kk = (double)K * (double)K;
-    for (int p = threadIdx.x >> 5; p < A.passes; p += blockDim.x >> 5) {
+    for (int p = threadIdx.x >> 5; p < P.passes; p += blockDim.x >> 5) {
         double sq = 0.0;
         for (int d = lane; d < 256; d += 32) {
             const double c = (double)__ldcg(A.hist + p * 256 + d);
@@ -115,17 +152,17 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const HistArgs A) {
 }
 
 struct PassArgs {
-    const uint64_t* kin;
-    const uint32_t* vin;
-    uint64_t* kout;
-    uint32_t* vout;
+    uint64_t* keys;  // buffer 0 (the result); buffer 1 follows at keys + kcap
+    uint32_t* vals;  // alike
+    int64_t kcap;
+    bool fused;
     uint32_t* status;
     const uint32_t* hist;   // this pass's 256 digit totals
     uint32_t* lookback;     // this pass's table [partitions][256]
     uint32_t* lookback_next;// next pass's table: this block clears its own row
     uint32_t* ticket;
     const uint32_t* method; // this pass's ranking method (set by sort_hist)
-    int shift, dbits;
+    int pass, tile_bits, dmax;
     uint32_t spin_limit;    // polls per look-back wait before it gives up
     int64_t withhold;       // partition that never publishes (wait-expiry test), else -1
 };
@@ -179,6 +216,16 @@ __device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long 
 
 __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassArgs A) {
     pdl_begin();
+    const DevPlan P = device_plan(A.status, A.tile_bits, A.dmax, A.fused);
+    if (A.pass >= P.passes) return;  // the plan needs fewer passes
+    // pass p reads buffer (start + p) mod 2 and writes the other one
+    const int64_t src = ((P.start + A.pass) & 1) ? A.kcap : 0;
+    const int64_t dst = A.kcap - src;
+    const uint64_t* kin = A.keys + src;
+    const uint32_t* vin = A.vals + src;
+    uint64_t* kout = A.keys + dst;
+    uint32_t* vout = A.vals + dst;
+    const int shift = A.pass * P.dbits;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PassSmem& S = *reinterpret_cast<PassSmem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -205,7 +252,9 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
     const uint32_t nparts = (K + kSortPartition - 1) / kSortPartition;
     if (part >= nparts) return;
     const uint32_t base = part * kSortPartition;
-    const uint32_t mask = (1u << A.dbits) - 1u;
+    const uint32_t mask = (1u << P.dbits) - 1u;
+    const bool first = A.pass == 0, last = A.pass == P.passes - 1;
+    auto digit = [&](uint64_t im) { return (uint32_t)((im >> shift) & mask); };
 
     // Load: warp w owns keys [base + 32 I w, base + 32 I (w+1)) (I items per
     // thread); round r reads 32 consecutive keys, so (warp, round, lane) order
@@ -216,8 +265,12 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
     for (int r = 0; r < kSortItems; ++r) {
         const uint32_t idx = base + warp * (kSortItems * 32) + r * 32 + lane;
         const bool ok = idx < K;
-        key[r] = ok ? A.kin[idx] : 0ull;
-        val[r] = ok ? A.vin[idx] : 0u;
+        key[r] = ok ? kin[idx] : 0ull;
+        val[r] = ok ? vin[idx] : 0u;
+    }
+    if (first) {
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) key[r] = plan_image(key[r], P);
     }
     // Rank within the warp, round by round: lanes with equal digits in a round
     // find each other (warp match, or each lane ORs its bit into its digit's
@@ -235,7 +288,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const uint32_t idx = base + warp * (kSortItems * 32) + r * 32 + lane;
-        const uint32_t d = idx < K ? (uint32_t)((key[r] >> A.shift) & mask) : kNoDigit;
+        const uint32_t d = idx < K ? digit(key[r]) : kNoDigit;
         uint32_t peers;
         if (by_match) {
             __syncwarp();
@@ -301,7 +354,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
     uint32_t pos[kSortItems];
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r)
-        pos[r] = rank[r] != kNoDigit ? S.wbase[warp][(uint32_t)(key[r] >> A.shift) & mask] + rank[r] : kNoDigit;
+        pos[r] = rank[r] != kNoDigit ? S.wbase[warp][digit(key[r])] + rank[r] : kNoDigit;
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         if (pos[r] != kNoDigit) {
@@ -353,12 +406,11 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
     __syncthreads();
     const uint32_t nvalid = min((uint32_t)kSortPartition, K - base);
     auto put = [&](uint32_t i) {
-        const uint64_t k = S.st.keys[i];
-        const uint32_t d = (uint32_t)((k >> A.shift) & mask);
-        const uint32_t o = S.gbase[d] + i;
+        const uint64_t im = S.st.keys[i];
+        const uint32_t o = S.gbase[digit(im)] + i;
         if (o < K) {  // always true unless a look-back wait timed out (flagged above)
-            A.kout[o] = k;
-            A.vout[o] = S.st.vals[i];
+            kout[o] = last ? plan_key(im, P) : im;
+            vout[o] = S.st.vals[i];
         }
     };
     if (nvalid == (uint32_t)kSortPartition) {
@@ -377,23 +429,15 @@ int sort_tile_bits(int64_t tiles) {
     return b;
 }
 
-// Even number of passes (the result returns to buffer 0) with at most 8 bits
-// per digit, or at most `digit_override` bits when it is 4..8.
-void sort_plan(int64_t tiles, int digit_override, int* passes, int* digit_bits) {
-    const int bits = 32 + sort_tile_bits(tiles);
-    const int dmax = (digit_override >= 4 && digit_override <= 8) ? digit_override : 8;
-    int p = (bits + dmax - 1) / dmax;
-    p += p & 1;
-    if (p > kMaxPasses) p = kMaxPasses;
-    *passes = p;
-    *digit_bits = (bits + p - 1) / p;
-}
 
 int64_t sort_partitions_for(int64_t kcap) { return (kcap + kSortPartition - 1) / kSortPartition; }
 
-gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override) {
-    int passes, dbits;
-    sort_plan((int64_t)v.gx * v.gy, digit_override, &passes, &dbits);
+gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override, bool fused) {
+    // at most 8 bits per digit, or at most digit_override when it is 4..8;
+    // launches for the longest plan (all 32 depth bits kept)
+    const int tile_bits = sort_tile_bits((int64_t)v.gx * v.gy);
+    const int dmax = sort_digit_max(digit_override);
+    const int passes = sort_max_passes(tile_bits, dmax, fused);
     static bool attr_done[64] = {false};
     if (!attr_done[ctx->device & 63]) {
         if (cudaFuncSetAttribute(sort_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -402,15 +446,18 @@ gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override) {
                              (int)sizeof(PassSmem));
         attr_done[ctx->device & 63] = true;
     }
-    // histograms and tickets start at zero
-    (void)launch_pdl(ctx->stream, zero_words_kernel, dim3(zero_blocks(kSortCtlWords)), dim3(256), 0, v.sort_hist,
-                     (int64_t)kSortCtlWords);
-    ctx->launches += 1;
+    // histograms and tickets start at zero (a fused chain's scan has cleared them)
+    if (!fused) {
+        (void)launch_pdl(ctx->stream, zero_words_kernel, dim3(zero_blocks(kSortCtlWords)), dim3(256), 0, v.sort_hist,
+                         (int64_t)kSortCtlWords);
+        ctx->launches += 1;
+    }
     if (v.kcap == 0) return GS_OK;
     const int64_t parts = sort_partitions_for(v.kcap);
     const size_t table = (size_t)v.sort_partitions * 256;
     uint32_t* method = v.sort_hist + kMaxPasses * 256 + kMaxPasses;
-    HistArgs H{v.keys0, v.status, v.sort_hist, v.sort_lookback, method, method + kMaxPasses, passes, dbits};
+    HistArgs H{v.keys0, v.kcap, fused, v.status, v.sort_hist, v.sort_lookback, method, method + kMaxPasses,
+               tile_bits, dmax};
     int hblocks = (int)std::min<int64_t>((v.kcap + 2047) / 2048, (int64_t)ctx->num_sms * 8);
     if (hblocks < 1) hblocks = 1;
     (void)launch_pdl(ctx->stream, sort_hist_kernel, dim3(hblocks), dim3(256), 0, H);
@@ -418,18 +465,19 @@ gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override) {
     for (int p = 0; p < passes; ++p) {
         PassArgs A;
         const bool even = (p % 2) == 0;
-        A.kin = even ? v.keys0 : v.keys1;
-        A.vin = even ? v.vals0 : v.vals1;
-        A.kout = even ? v.keys1 : v.keys0;
-        A.vout = even ? v.vals1 : v.vals0;
+        A.keys = v.keys0;
+        A.vals = v.vals0;
+        A.kcap = v.kcap;
+        A.fused = fused;
         A.status = v.status;
         A.hist = v.sort_hist + p * 256;
         A.lookback = v.sort_lookback + (even ? 0 : table);
         A.lookback_next = (p + 1 < passes) ? v.sort_lookback + (even ? table : 0) : nullptr;
         A.ticket = v.sort_hist + kMaxPasses * 256 + p;
         A.method = method + p;
-        A.shift = p * dbits;
-        A.dbits = dbits;
+        A.pass = p;
+        A.tile_bits = tile_bits;
+        A.dmax = dmax;
         A.spin_limit = ctx->sort_spin_limit;
         A.withhold = ctx->sort_withhold;
         (void)launch_pdl(ctx->stream, sort_pass_kernel, dim3((unsigned)parts), dim3(kSortThreads), sizeof(PassSmem), A);

@@ -19,6 +19,7 @@ MODES = {"3sigma": 0, "snugbox": 1, "accutile": 2, "tbc": 3, "pixel": 4}
 MODE_NAMES = {v: k for k, v in MODES.items()}
 FLAG_CAPACITY = 1
 FLAG_TIMEOUT = 2
+FLAG_KEYRANGE = 8
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID", 2: "GS_ERR_OOM", 3: "GS_ERR_CAPACITY", 4: "GS_ERR_CUDA",
                 5: "GS_ERR_TIMEOUT"}
 MAX_KEYS = (1 << 30) - 1
@@ -73,7 +74,7 @@ EXPORTS = ["gs_create", "gs_destroy", "gs_set_stream", "gs_last_error", "gs_laun
            "gs_preprocess", "gs_intersect", "gs_sort", "gs_tile_ranges", "gs_render", "gs_render_stats",
            "gs_forward", "gs_read_status", "gs_backward_work_bytes", "gs_render_backward", "gs_intersect_noalloc",
            "gs_batch_sizes", "gs_forward_batch", "gs_batch_status", "gs_read_culled", "gs_set_sort_wait",
-           "gs_pup_work_bytes", "gs_pup_accumulate", "gs_pup_score"]
+           "gs_pup_work_bytes", "gs_pup_accumulate", "gs_pup_score", "gs_read_sort_plan"]
 
 _lib = None
 
@@ -104,6 +105,8 @@ def load(path=None) -> ctypes.CDLL:
         getattr(L, name).argtypes = [P, POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame)]
     L.gs_forward.argtypes = [P, POINTER(GsScene), POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame)]
     L.gs_read_status.argtypes = [P, POINTER(GsFrame), POINTER(c_int64), POINTER(c_uint32)]
+    L.gs_read_sort_plan.argtypes = [P, POINTER(GsRasterCfg), POINTER(GsFrame), POINTER(c_int32), POINTER(c_int32),
+                                    POINTER(c_int32)]
     L.gs_render_stats.argtypes = [P, POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame),
                                   POINTER(ctypes.c_uint64), POINTER(ctypes.c_uint64), POINTER(ctypes.c_uint64)]
     L.gs_backward_work_bytes.argtypes = [c_int64]
@@ -365,11 +368,18 @@ class Rasterizer:
     def gs_set_sort_wait(self, max_polls: int = 0, withhold_partition: int = -1):
         self._check(self.lib.gs_set_sort_wait(self.ctx, int(max_polls), int(withhold_partition)), "gs_set_sort_wait")
 
+    def gs_read_sort_plan(self, cfg, frame: Frame):
+        """(passes, digit_bits, depth_bits) of gs_sort for the frame's last emitted keys."""
+        p, d, w = c_int32(0), c_int32(0), c_int32(0)
+        self._check(self.lib.gs_read_sort_plan(self.ctx, ctypes.byref(cfg), ctypes.byref(frame.struct),
+                                               ctypes.byref(p), ctypes.byref(d), ctypes.byref(w)), "gs_read_sort_plan")
+        return int(p.value), int(d.value), int(w.value)
+
     def gs_read_status(self, frame: Frame, raise_on_error: bool = True):
         k = c_int64(0)
         fl = c_uint32(0)
         st = self.lib.gs_read_status(self.ctx, ctypes.byref(frame.struct), ctypes.byref(k), ctypes.byref(fl))
-        if st != 0 and (raise_on_error or st not in (3, 5) or not fl.value):
+        if st != 0 and (raise_on_error or st not in (1, 3, 5) or not fl.value):
             self._check(st, "gs_read_status")  # CUDA errors always raise
         return int(k.value), int(fl.value)
 

@@ -73,6 +73,47 @@ def test_sort_wait_runs_out_then_context_recovers(raster):
     assert np.abs(frame.image.cpu().numpy().astype(np.float64) - ref["image"]).max() <= 1e-4
 
 
+def test_sort_rejects_keys_outside_the_recorded_range(raster):
+    """gs_sort orders keys by (tile, depth bits - least depth bits) over the
+    span gs_intersect recorded; a key changed after the emit to lie below that
+    span is reported (GS_FLAG_KEYRANGE, GS_ERR_INVALID), the later stages see
+    no keys, and the next frame renders normally."""
+    scene, cam = synth.small_box_workload()
+    ref = oracle.render(scene, cam, 16, 2, bg=BG, prec64=False)
+    K = ref["num_keys"]
+    rast = raster.Rasterizer("cuda:0")
+    ds = scene.to("cuda:0")
+    cfg = raster.cfg_struct(16, "accutile", BG)
+    frame = raster.Frame(scene.n, cam.width, cam.height, 16, K + 100, "cuda:0")
+    rast.gs_preprocess(ds, cam, cfg, frame)
+    rast.gs_intersect(cam, cfg, frame)
+    passes, _, w = rast.gs_read_sort_plan(cfg, frame)
+    assert w < 32 and passes < 6
+    torch.cuda.synchronize()
+    keys = frame.keys[:K].view(torch.int64)
+    keys[K // 2] = keys[K // 2] & ~0xFFFFFFFF  # depth bits 0: below every recorded depth
+    torch.cuda.synchronize()
+    rast.gs_sort(cam, cfg, frame)
+    rast.gs_tile_ranges(cam, cfg, frame)
+    rast.gs_render(cam, cfg, frame)
+    k, flags = rast.gs_read_status(frame, raise_on_error=False)
+    assert flags & raster.FLAG_KEYRANGE and k == K
+    with pytest.raises(raster.GsError) as ei:
+        rast.gs_read_status(frame)
+    assert ei.value.status == 1  # GS_ERR_INVALID
+    assert int(frame.tile_ranges().abs().sum()) == 0
+    img = frame.image.cpu().numpy()
+    for c in range(3):
+        assert np.all(img[c] == np.float32(BG[c]))
+
+    forward(raster, rast, ds, cam, cfg, frame)
+    k, flags = rast.gs_read_status(frame)
+    assert flags == 0 and k == K
+    assert np.array_equal(frame.keys[:K].cpu().numpy().view(np.uint64), ref["keys"])
+    assert np.array_equal(frame.vals[:K].cpu().numpy().view(np.uint32), ref["vals"])
+    assert np.abs(frame.image.cpu().numpy().astype(np.float64) - ref["image"]).max() <= 1e-4
+
+
 def poisoned_scene():
     scene = synth.uniform_box_scene(3000, seed=41, log_scale_mu=-3.0)
     nan, inf = float("nan"), float("inf")

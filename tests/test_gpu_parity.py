@@ -33,6 +33,22 @@ def rast(raster):
     return raster.Rasterizer("cuda:0")
 
 
+def expected_sort_plan(keys, tiles, sort_digit_bits):
+    """The sort's plan for these keys: the tile bits, the bit length of the
+    span of their depth bits (all 32 without keys), at most 8 (or the
+    override's) bits per digit, 2 to 12 passes, digits as even as they go."""
+    tile_bits = max(int(tiles) - 1, 0).bit_length()
+    if len(keys):
+        d = (keys & np.uint64(0xFFFFFFFF)).astype(np.int64)
+        w = int(d.max() - d.min()).bit_length()
+    else:
+        w = 32
+    dmax = sort_digit_bits if 4 <= sort_digit_bits <= 8 else 8
+    total = tile_bits + w
+    passes = min(max(-(-total // dmax), 2), 12)
+    return passes, -(-total // passes), w
+
+
 def run_pipeline(raster, rast, scene, cam, mode, tile, bg=(0.0, 0.0, 0.0), n_capacity=None, key_capacity=None,
                  sort_digit_bits=0):
     """Run the five stages through the C ABI, snapshotting each stage's output."""
@@ -53,6 +69,10 @@ def run_pipeline(raster, rast, scene, cam, mode, tile, bg=(0.0, 0.0, 0.0), n_cap
     Ke = min(K, key_capacity)
     out["keys_unsorted"] = frame.keys[:Ke].cpu().numpy().view(np.uint64).copy()
     out["vals_unsorted"] = frame.vals[:Ke].cpu().numpy().view(np.uint32).copy()
+    if K <= key_capacity:
+        # the sort keeps only the depth bits the emitted keys span
+        tiles = -(-cam.width // tile) * -(-cam.height // tile)
+        assert rast.gs_read_sort_plan(cfg, frame) == expected_sort_plan(out["keys_unsorted"], tiles, sort_digit_bits)
     rast.gs_sort(cam, cfg, frame)
     rast.gs_tile_ranges(cam, cfg, frame)
     rast.gs_render(cam, cfg, frame)
