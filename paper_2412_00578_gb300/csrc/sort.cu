@@ -229,195 +229,201 @@ __global__ void __launch_bounds__(kSortThreads, 2) sort_pass_kernel(const PassAr
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PassSmem& S = *reinterpret_cast<PassSmem*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) S.part = atomicAdd(A.ticket, 1u);
     const bool by_match = __ldg(A.method) == kRankMatch;  // uniform over the launch
     const uint32_t t = tid;
     const bool digit_thread = t < 256;
     const uint32_t hist_t = digit_thread ? __ldg(A.hist + t) : 0u;  // loaded early, used after ranking
-    {
-        uint4* c4 = reinterpret_cast<uint4*>(&S.wbase[0][0]);
-        constexpr int n4 = (int)(sizeof(S.wbase) / sizeof(uint4));
-#pragma unroll
-        for (int i = tid; i < n4; i += kSortThreads) c4[i] = make_uint4(0u, 0u, 0u, 0u);
-        if (!by_match) {
-            uint4* p4 = reinterpret_cast<uint4*>(&S.peer[0][0][0]);
-            constexpr int np4 = (int)(sizeof(S.peer) / sizeof(uint4));
-#pragma unroll
-            for (int i = tid; i < np4; i += kSortThreads) p4[i] = make_uint4(0u, 0u, 0u, 0u);
-        }
-    }
-    __syncthreads();
     const uint32_t K = frame_keys(A.status);
-    const uint32_t part = S.part;
     const uint32_t nparts = (K + kSortPartition - 1) / kSortPartition;
-    if (part >= nparts) return;
-    const uint32_t base = part * kSortPartition;
-    const uint32_t mask = (1u << P.dbits) - 1u;
-    const bool first = A.pass == 0, last = A.pass == P.passes - 1;
-    auto digit = [&](uint64_t im) { return (uint32_t)((im >> shift) & mask); };
+    // Persistent: at most two CTAs per SM, each taking partitions by ticket
+    // until none is left.  A ticket's predecessors are held by CTAs that are
+    // running or done, so every look-back wait ends.
+    for (;;) {
+        if (tid == 0) S.part = atomicAdd(A.ticket, 1u);
+        {
+            uint4* c4 = reinterpret_cast<uint4*>(&S.wbase[0][0]);
+            constexpr int n4 = (int)(sizeof(S.wbase) / sizeof(uint4));
+#pragma unroll
+            for (int i = tid; i < n4; i += kSortThreads) c4[i] = make_uint4(0u, 0u, 0u, 0u);
+            if (!by_match) {
+                uint4* p4 = reinterpret_cast<uint4*>(&S.peer[0][0][0]);
+                constexpr int np4 = (int)(sizeof(S.peer) / sizeof(uint4));
+#pragma unroll
+                for (int i = tid; i < np4; i += kSortThreads) p4[i] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+        __syncthreads();
+        const uint32_t part = S.part;
+        if (part >= nparts) break;
+        const uint32_t base = part * kSortPartition;
+        const uint32_t mask = (1u << P.dbits) - 1u;
+        const bool first = A.pass == 0, last = A.pass == P.passes - 1;
+        auto digit = [&](uint64_t im) { return (uint32_t)((im >> shift) & mask); };
 
-    // Load: warp w owns keys [base + 32 I w, base + 32 I (w+1)) (I items per
-    // thread); round r reads 32 consecutive keys, so (warp, round, lane) order
-    // is input order.
-    uint64_t key[kSortItems];
-    uint32_t val[kSortItems];
+        // Load: warp w owns keys [base + 32 I w, base + 32 I (w+1)) (I items per
+        // thread); round r reads 32 consecutive keys, so (warp, round, lane) order
+        // is input order.
+        uint64_t key[kSortItems];
+        uint32_t val[kSortItems];
 #pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        const uint32_t idx = base + warp * (kSortItems * 32) + r * 32 + lane;
-        const bool ok = idx < K;
-        key[r] = ok ? kin[idx] : 0ull;
-        val[r] = ok ? vin[idx] : 0u;
-    }
-    if (first) {
-#pragma unroll
-        for (int r = 0; r < kSortItems; ++r) key[r] = plan_image(key[r], P);
-    }
-    // Rank within the warp, round by round: lanes with equal digits in a round
-    // find each other (warp match, or each lane ORs its bit into its digit's
-    // word and reads the word back); the lowest of them adds the group's size
-    // to the warp's counter for that digit, and the counter's old value plus
-    // the number of lower lanes in the group is each key's rank among the
-    // warp's keys with that digit.  A __syncwarp separates one round's
-    // counter updates from the next round's.  With atomicOr, round r uses
-    // array r mod 3 and clears its words of round r-1 after the round's
-    // __syncwarp (every lane has read them before it), so an array is clean
-    // again, behind another __syncwarp, when round r+2 uses it.
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    uint32_t rank[kSortItems];  // kNoDigit past the last key
-    uint32_t dprev = kNoDigit;
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        const uint32_t idx = base + warp * (kSortItems * 32) + r * 32 + lane;
-        const uint32_t d = idx < K ? digit(key[r]) : kNoDigit;
-        uint32_t peers;
-        if (by_match) {
-            __syncwarp();
-            peers = __match_any_sync(0xffffffffu, d);
-        } else {
-            if (d != kNoDigit) atomicOr(&S.peer[warp][r % 3][d], 1u << lane);
-            __syncwarp();
-            peers = d != kNoDigit ? S.peer[warp][r % 3][d] : 0u;
-            if (dprev != kNoDigit) S.peer[warp][(r + 2) % 3][dprev] = 0u;
-            dprev = d;
+        for (int r = 0; r < kSortItems; ++r) {
+            const uint32_t idx = base + warp * (kSortItems * 32) + r * 32 + lane;
+            const bool ok = idx < K;
+            key[r] = ok ? kin[idx] : 0ull;
+            val[r] = ok ? vin[idx] : 0u;
         }
-        const uint32_t lt = __popc(peers & lt_mask);
-        uint32_t before = 0u;
-        if (d != kNoDigit && lt == 0) before = atomicAdd(&S.wbase[warp][d], (uint32_t)__popc(peers));
-        const int leader = peers ? __ffs(peers) - 1 : lane;
-        before = __shfl_sync(0xffffffffu, before, leader);
-        rank[r] = d != kNoDigit ? before + lt : kNoDigit;
-    }
-    __syncthreads();
-    // Per digit (threads 0..255, thread t <-> digit t): block total and
-    // published aggregate.  The other threads feed zeros to the block scan.
-    uint32_t tot = 0;
-    if (digit_thread) {
+        if (first) {
 #pragma unroll
-        for (int w = 0; w < kSortThreads / 32; ++w) tot += S.wbase[w][t];
-        if ((int64_t)part != A.withhold)
-            st_relaxed_gpu(A.lookback + (size_t)part * 256 + t, (part == 0 ? kFlagPrefix : kFlagAgg) | tot);
-        // clear this partition's row of the next pass's table (that table's last
-        // user was the previous pass, which has completed)
-        if (A.lookback_next) A.lookback_next[(size_t)part * 256 + t] = 0;
-    }
-    // one scan for both the block's digit offsets (low 16 bits, at most 4096)
-    // and the digits' global starts (high bits)
-    const unsigned long long packed =
-        ((unsigned long long)hist_t << 16) | (unsigned long long)tot;
-    const unsigned long long sc = block_excl_scan_u64(packed, S.warp_tmp);
-    const uint32_t boff = (uint32_t)(sc & 0xffffull);
-    const uint32_t dstart = (uint32_t)(sc >> 16);
-    // Per digit: the staging slot of each warp's first key with the digit.
-    // The counters are read in batches of 8 warps ahead of the stores: the
-    // compiler cannot tell that the stores miss the words still to be read,
-    // so a read after a store would wait for it.
-    if (digit_thread) {
-        constexpr int kBatch = 8;
-        static_assert((kSortThreads / 32) % kBatch == 0, "warps come in batches of 8");
-        uint32_t run = boff;
+            for (int r = 0; r < kSortItems; ++r) key[r] = plan_image(key[r], P);
+        }
+        // Rank within the warp, round by round: lanes with equal digits in a round
+        // find each other (warp match, or each lane ORs its bit into its digit's
+        // word and reads the word back); the lowest of them adds the group's size
+        // to the warp's counter for that digit, and the counter's old value plus
+        // the number of lower lanes in the group is each key's rank among the
+        // warp's keys with that digit.  A __syncwarp separates one round's
+        // counter updates from the next round's.  With atomicOr, round r uses
+        // array r mod 3 and clears its words of round r-1 after the round's
+        // __syncwarp (every lane has read them before it), so an array is clean
+        // again, behind another __syncwarp, when round r+2 uses it.
+        const uint32_t lt_mask = (1u << lane) - 1u;
+        uint32_t rank[kSortItems];  // kNoDigit past the last key
+        uint32_t dprev = kNoDigit;
 #pragma unroll
-        for (int w0 = 0; w0 < kSortThreads / 32; w0 += kBatch) {
-            uint32_t c[kBatch];
-#pragma unroll
-            for (int w = 0; w < kBatch; ++w) c[w] = S.wbase[w0 + w][t];
-#pragma unroll
-            for (int w = 0; w < kBatch; ++w) {
-                S.wbase[w0 + w][t] = run;
-                run += c[w];
+        for (int r = 0; r < kSortItems; ++r) {
+            const uint32_t idx = base + warp * (kSortItems * 32) + r * 32 + lane;
+            const uint32_t d = idx < K ? digit(key[r]) : kNoDigit;
+            uint32_t peers;
+            if (by_match) {
+                __syncwarp();
+                peers = __match_any_sync(0xffffffffu, d);
+            } else {
+                if (d != kNoDigit) atomicOr(&S.peer[warp][r % 3][d], 1u << lane);
+                __syncwarp();
+                peers = d != kNoDigit ? S.peer[warp][r % 3][d] : 0u;
+                if (dprev != kNoDigit) S.peer[warp][(r + 2) % 3][dprev] = 0u;
+                dprev = d;
             }
+            const uint32_t lt = __popc(peers & lt_mask);
+            uint32_t before = 0u;
+            if (d != kNoDigit && lt == 0) before = atomicAdd(&S.wbase[warp][d], (uint32_t)__popc(peers));
+            const int leader = peers ? __ffs(peers) - 1 : lane;
+            before = __shfl_sync(0xffffffffu, before, leader);
+            rank[r] = d != kNoDigit ? before + lt : kNoDigit;
         }
-    }
-    __syncthreads();
-    // Stage in digit order (positions are block-local, so this does not wait
-    // for the look-back, and it frees the key registers before it).  All
-    // positions are computed before the first store, so the reads overlap.
-    uint32_t pos[kSortItems];
+        __syncthreads();
+        // Per digit (threads 0..255, thread t <-> digit t): block total and
+        // published aggregate.  The other threads feed zeros to the block scan.
+        uint32_t tot = 0;
+        if (digit_thread) {
 #pragma unroll
-    for (int r = 0; r < kSortItems; ++r)
-        pos[r] = rank[r] != kNoDigit ? S.wbase[warp][digit(key[r])] + rank[r] : kNoDigit;
-#pragma unroll
-    for (int r = 0; r < kSortItems; ++r) {
-        if (pos[r] != kNoDigit) {
-            S.st.keys[pos[r]] = key[r];
-            S.st.vals[pos[r]] = val[r];
-        }
-    }
-    if (digit_thread) {
-        uint32_t prefix = 0;
-        if (part > 0) {
-            // Look back over the predecessors' published words, kLookWindow at
-            // a time (all loads in flight together): add aggregates until an
-            // inclusive prefix is found; on a word not yet published, poll it
-            // again (bounded).
-            int64_t j = (int64_t)part - 1;
-            uint32_t spins = 0;
-            bool found = false;
-            while (!found && j >= 0) {
-                uint32_t w[kLookWindow];
-#pragma unroll
-                for (int m = 0; m < kLookWindow; ++m)
-                    w[m] = (j - m >= 0) ? ld_relaxed_gpu(A.lookback + (size_t)(j - m) * 256 + t) : kFlagPrefix;
-                int m = 0;  // words consumed from this window
-#pragma unroll
-                for (int mm = 0; mm < kLookWindow; ++mm) {
-                    const uint32_t flag = w[mm] & ~kCountMask;
-                    if (flag == 0) break;  // not yet published: poll again from here
-                    prefix += w[mm] & kCountMask;
-                    ++m;
-                    if (flag == kFlagPrefix) {
-                        found = true;
-                        break;
-                    }
-                }
-                j -= m;
-                if (!found && m < kLookWindow && j >= 0) {
-                    if (++spins > A.spin_limit) {
-                        atomicOr(A.status + 2, GS_FLAG_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-            }
+            for (int w = 0; w < kSortThreads / 32; ++w) tot += S.wbase[w][t];
             if ((int64_t)part != A.withhold)
-                st_relaxed_gpu(A.lookback + (size_t)part * 256 + t, kFlagPrefix | (prefix + tot));
+                st_relaxed_gpu(A.lookback + (size_t)part * 256 + t, (part == 0 ? kFlagPrefix : kFlagAgg) | tot);
+            // clear this partition's row of the next pass's table (that table's last
+            // user was the previous pass, which has completed)
+            if (A.lookback_next) A.lookback_next[(size_t)part * 256 + t] = 0;
         }
-        S.gbase[t] = dstart + prefix - boff;  // modular: gbase + staging index = output index
-    }
-    __syncthreads();
-    const uint32_t nvalid = min((uint32_t)kSortPartition, K - base);
-    auto put = [&](uint32_t i) {
-        const uint64_t im = S.st.keys[i];
-        const uint32_t o = S.gbase[digit(im)] + i;
-        if (o < K) {  // always true unless a look-back wait timed out (flagged above)
-            kout[o] = last ? plan_key(im, P) : im;
-            vout[o] = S.st.vals[i];
-        }
-    };
-    if (nvalid == (uint32_t)kSortPartition) {
+        // one scan for both the block's digit offsets (low 16 bits, at most 4096)
+        // and the digits' global starts (high bits)
+        const unsigned long long packed =
+            ((unsigned long long)hist_t << 16) | (unsigned long long)tot;
+        const unsigned long long sc = block_excl_scan_u64(packed, S.warp_tmp);
+        const uint32_t boff = (uint32_t)(sc & 0xffffull);
+        const uint32_t dstart = (uint32_t)(sc >> 16);
+        // Per digit: the staging slot of each warp's first key with the digit.
+        // The counters are read in batches of 8 warps ahead of the stores: the
+        // compiler cannot tell that the stores miss the words still to be read,
+        // so a read after a store would wait for it.
+        if (digit_thread) {
+            constexpr int kBatch = 8;
+            static_assert((kSortThreads / 32) % kBatch == 0, "warps come in batches of 8");
+            uint32_t run = boff;
 #pragma unroll
-        for (int u = 0; u < kSortItems; ++u) put(tid + (uint32_t)u * kSortThreads);
-    } else {
-        for (uint32_t i = tid; i < nvalid; i += kSortThreads) put(i);
+            for (int w0 = 0; w0 < kSortThreads / 32; w0 += kBatch) {
+                uint32_t c[kBatch];
+#pragma unroll
+                for (int w = 0; w < kBatch; ++w) c[w] = S.wbase[w0 + w][t];
+#pragma unroll
+                for (int w = 0; w < kBatch; ++w) {
+                    S.wbase[w0 + w][t] = run;
+                    run += c[w];
+                }
+            }
+        }
+        __syncthreads();
+        // Stage in digit order (positions are block-local, so this does not wait
+        // for the look-back, and it frees the key registers before it).  All
+        // positions are computed before the first store, so the reads overlap.
+        uint32_t pos[kSortItems];
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r)
+            pos[r] = rank[r] != kNoDigit ? S.wbase[warp][digit(key[r])] + rank[r] : kNoDigit;
+#pragma unroll
+        for (int r = 0; r < kSortItems; ++r) {
+            if (pos[r] != kNoDigit) {
+                S.st.keys[pos[r]] = key[r];
+                S.st.vals[pos[r]] = val[r];
+            }
+        }
+        if (digit_thread) {
+            uint32_t prefix = 0;
+            if (part > 0) {
+                // Look back over the predecessors' published words, kLookWindow at
+                // a time (all loads in flight together): add aggregates until an
+                // inclusive prefix is found; on a word not yet published, poll it
+                // again (bounded).
+                int64_t j = (int64_t)part - 1;
+                uint32_t spins = 0;
+                bool found = false;
+                while (!found && j >= 0) {
+                    uint32_t w[kLookWindow];
+#pragma unroll
+                    for (int m = 0; m < kLookWindow; ++m)
+                        w[m] = (j - m >= 0) ? ld_relaxed_gpu(A.lookback + (size_t)(j - m) * 256 + t) : kFlagPrefix;
+                    int m = 0;  // words consumed from this window
+#pragma unroll
+                    for (int mm = 0; mm < kLookWindow; ++mm) {
+                        const uint32_t flag = w[mm] & ~kCountMask;
+                        if (flag == 0) break;  // not yet published: poll again from here
+                        prefix += w[mm] & kCountMask;
+                        ++m;
+                        if (flag == kFlagPrefix) {
+                            found = true;
+                            break;
+                        }
+                    }
+                    j -= m;
+                    if (!found && m < kLookWindow && j >= 0) {
+                        if (++spins > A.spin_limit) {
+                            atomicOr(A.status + 2, GS_FLAG_TIMEOUT);
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                }
+                if ((int64_t)part != A.withhold)
+                    st_relaxed_gpu(A.lookback + (size_t)part * 256 + t, kFlagPrefix | (prefix + tot));
+            }
+            S.gbase[t] = dstart + prefix - boff;  // modular: gbase + staging index = output index
+        }
+        __syncthreads();
+        const uint32_t nvalid = min((uint32_t)kSortPartition, K - base);
+        auto put = [&](uint32_t i) {
+            const uint64_t im = S.st.keys[i];
+            const uint32_t o = S.gbase[digit(im)] + i;
+            if (o < K) {  // always true unless a look-back wait timed out (flagged above)
+                kout[o] = last ? plan_key(im, P) : im;
+                vout[o] = S.st.vals[i];
+            }
+        };
+        if (nvalid == (uint32_t)kSortPartition) {
+#pragma unroll
+            for (int u = 0; u < kSortItems; ++u) put(tid + (uint32_t)u * kSortThreads);
+        } else {
+            for (uint32_t i = tid; i < nvalid; i += kSortThreads) put(i);
+        }
+        __syncthreads();  // the next partition reuses the staging memory
     }
 }
 
@@ -453,7 +459,8 @@ gs_status launch_sort(gs_context* ctx, const FrameView& v, int digit_override, b
         ctx->launches += 1;
     }
     if (v.kcap == 0) return GS_OK;
-    const int64_t parts = sort_partitions_for(v.kcap);
+    // persistent pass grid: two CTAs per SM at most, never more than the partitions
+    const int64_t parts = std::min<int64_t>(sort_partitions_for(v.kcap), (int64_t)ctx->num_sms * 2);
     const size_t table = (size_t)v.sort_partitions * 256;
     uint32_t* method = v.sort_hist + kMaxPasses * 256 + kMaxPasses;
     HistArgs H{v.keys0, v.kcap, fused, v.status, v.sort_hist, v.sort_lookback, method, method + kMaxPasses,
