@@ -395,13 +395,14 @@ def test_outdoor_pruned_300k(raster, outdoor):
 
 
 # ---------------------------------------------------------------- gs_forward
-def run_forward(raster, rast, scene, cam, mode, tile, bg=(0.0, 0.0, 0.0), key_capacity=None, n_capacity=None):
+def run_forward(raster, rast, scene, cam, mode, tile, bg=(0.0, 0.0, 0.0), key_capacity=None, n_capacity=None,
+                sort_digit_bits=0):
     """gs_forward: the five stages in one call, launched as one chain."""
     ncap = scene.n if n_capacity is None else n_capacity
     if key_capacity is None:
         key_capacity = max(oracle.count_keys(scene, cam, tile, mode, prec64=False), 1)
     frame = raster.Frame(ncap, cam.width, cam.height, tile, key_capacity, "cuda:0")
-    cfg = raster.cfg_struct(tile, mode, bg)
+    cfg = raster.cfg_struct(tile, mode, bg, sort_digit_bits)
     rast.gs_forward(scene.to("cuda:0"), cam, cfg, frame)
     K, flags = rast.gs_read_status(frame, raise_on_error=False)
     return frame, K, flags
@@ -434,6 +435,33 @@ def check_forward(raster, rast, scene, cam, mode, tile, bg=(0.0, 0.0, 0.0), **kw
 def test_forward_ragged(raster, rast, mode, tile):
     scene, cam = ragged_case()
     check_forward(raster, rast, scene, cam, mode, tile, bg=(0.1, 0.2, 0.3))
+
+
+@pytest.mark.parametrize("digits", [0, 7, 6, 5, 4])
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_forward_sort_plans(raster, rast, digits, tile):
+    """gs_forward's sort plan, chosen on the device from the recorded depth
+    range, at every digit width: odd pass counts (the emit writes buffer 1 so
+    the last pass ends in buffer 0) and even ones give the oracle's sorted
+    pairs, ranges and image, and the plan is the one the keys imply."""
+    scene, cam = synth.small_box_workload()
+    frame, K = check_forward(raster, rast, scene, cam, 2, tile, sort_digit_bits=digits)
+    cfg = raster.cfg_struct(tile, 2, (0.0, 0.0, 0.0), digits)
+    keys = oracle.render(scene, cam, tile, 2, prec64=False)["keys"]
+    tiles = -(-cam.width // tile) * -(-cam.height // tile)
+    assert rast.gs_read_sort_plan(cfg, frame) == expected_sort_plan(keys, tiles, digits)
+
+
+def test_forward_sort_plans_cover_both_parities():
+    """The plans of test_forward_sort_plans include odd and even pass counts."""
+    scene, cam = synth.small_box_workload()
+    parities = set()
+    for tile in (8, 16, 32):
+        keys = oracle.render(scene, cam, tile, 2, prec64=False)["keys"]
+        tiles = -(-cam.width // tile) * -(-cam.height // tile)
+        for digits in (0, 7, 6, 5, 4):
+            parities.add(expected_sort_plan(keys, tiles, digits)[0] % 2)
+    assert parities == {0, 1}
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
