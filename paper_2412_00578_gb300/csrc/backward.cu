@@ -49,7 +49,7 @@ struct BwdArgs {
 // and w_p = sum_ch (dC_ch/dg)^2 (zero where alpha is clamped), into a
 // 16-float row.
 template <int T, bool kPup>
-__global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 3 : 12)) blend_backward_kernel(const BwdArgs A) {
+__global__ void __launch_bounds__(T* T, T == 32 ? 1 : (T == 16 ? 4 : 12)) blend_backward_kernel(const BwdArgs A) {
     constexpr int kNV = kPup ? 15 : kWork;       // values per (pixel, Gaussian) pair
     constexpr int kRow = kPup ? 16 : kWorkRow;   // floats per Gaussian row
     constexpr int NT = T * T;
@@ -523,7 +523,7 @@ struct PupArgs {
     float* hessian;     // [21][n], +=
 };
 
-__global__ void __launch_bounds__(256) pup_jacobian_kernel(const PupArgs A) {
+__global__ void __launch_bounds__(256, 3) pup_jacobian_kernel(const PupArgs A) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.n || A.counts[i] <= 0) return;
     const int64_t n = A.n;
@@ -580,38 +580,79 @@ __global__ void __launch_bounds__(256) pup_jacobian_kernel(const PupArgs A) {
         }
 }
 
-// U_i = log det H_i by a Cholesky factorisation in double precision; -inf
-// where H_i is not positive definite (e.g. a Gaussian seen from one view
-// only: its 6 x 6 block has rank 5 at most).
+// U_i = log det H_i in double precision, by an LDL^T factorisation (no
+// square roots): the pivots d_j are positive exactly when H_i is positive
+// definite, and log det H_i = sum_j log d_j, taken as one logarithm of the
+// pivots' mantissa product (each in [1/2, 1), so no underflow) plus their
+// summed binary exponents times ln 2.  One reciprocal per pivot replaces the
+// divisions.  -inf where H_i is not positive definite (e.g. a Gaussian seen
+// from one view only: its 6 x 6 block has rank 5 at most).
 __global__ void __launch_bounds__(256) pup_logdet_kernel(const float* __restrict__ hessian, int64_t n,
                                                         float* __restrict__ score) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double H[6][6];
-    int e = 0;
-    for (int a = 0; a < 6; ++a)
-        for (int b = a; b < 6; ++b) {
-            H[a][b] = H[b][a] = (double)hessian[(int64_t)e * n + i];
-            ++e;
-        }
-    double logdet = 0.0;
-    bool pd = true;
-    for (int j = 0; j < 6 && pd; ++j) {
-        double d = H[j][j];
-        for (int k = 0; k < j; ++k) d -= H[j][k] * H[j][k];
-        if (!(d > 0.0)) {
-            pd = false;
-            break;
-        }
-        const double l = sqrt(d);
-        H[j][j] = l;
-        logdet += 2.0 * log(l);
-        for (int r = j + 1; r < 6; ++r) {
-            double v = H[r][j];
-            for (int k = 0; k < j; ++k) v -= H[r][k] * H[j][k];
-            H[r][j] = v / l;
+    // A positive definite matrix has a positive diagonal: checked from the
+    // six diagonal entries alone (entry (a, a) is row a's first of the packed
+    // upper triangle), which settles every Gaussian no view reached (H = 0).
+    // The rest of the block's Gaussians are factorised by its lowest threads,
+    // so the FP64 work runs in full warps.
+    __shared__ uint32_t s_idx[256];
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x;
+    {
+        const int64_t j = base + threadIdx.x;
+        if (j < n) {
+            bool diag = true;
+            constexpr int kDiag[6] = {0, 6, 11, 15, 18, 20};
+#pragma unroll
+            for (int a = 0; a < 6; ++a) diag = diag && (hessian[(int64_t)kDiag[a] * n + j] > 0.0f);
+            if (diag) s_idx[atomicAdd(&s_cnt, 1)] = threadIdx.x;
+            else score[j] = -INFINITY;
         }
     }
+    __syncthreads();
+    if ((int)threadIdx.x >= s_cnt) return;
+    const int64_t i = base + s_idx[threadIdx.x];
+    double A[6][6];
+    {
+        int e = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+            for (int b = a; b < 6; ++b) {
+                A[b][a] = (double)hessian[(int64_t)e * n + i];  // lower triangle
+                ++e;
+            }
+    }
+    double L[6][6];  // unit lower triangular factor (below the diagonal)
+    double d[6];
+    bool pd = true;
+    double mant = 1.0;
+    int expo = 0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        double v[6];  // v_k = L[j][k] d_k
+#pragma unroll
+        for (int k = 0; k < j; ++k) v[k] = L[j][k] * d[k];
+        double dj = A[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) dj = fma(-L[j][k], v[k], dj);
+        pd = pd && (dj > 0.0);
+        d[j] = dj;
+        int ej;
+        const double mj = frexp(dj, &ej);
+        mant *= mj;
+        expo += ej;
+        const double inv = __drcp_rn(dj);
+#pragma unroll
+        for (int r = j + 1; r < 6; ++r) {
+            double x = A[r][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) x = fma(-L[r][k], v[k], x);
+            L[r][j] = x * inv;
+        }
+    }
+    const double logdet = log(mant) + (double)expo * 0.69314718055994530942;
     score[i] = pd ? (float)logdet : -INFINITY;
 }
 
@@ -670,7 +711,7 @@ gs_status launch_pup(gs_context* ctx, const gs_scene* s, const gs_camera* cam, c
 
 gs_status launch_pup_score(gs_context* ctx, const float* hessian, int64_t n, float* score) {
     if (n == 0) return GS_OK;
-    pup_logdet_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(hessian, n, score);
+    pup_logdet_kernel<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(hessian, n, score);  // 256: s_idx
     ctx->launches += 1;
     return check_launch(ctx, "pup logdet");
 }
