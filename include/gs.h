@@ -92,9 +92,10 @@ typedef struct gs_camera {
 } gs_camera;
 
 /* Raster configuration: tile edge (8, 16 or 32 pixels), gs_mode, background,
- * and the radix sort's digit width (0 = automatic: the fewest even number of
- * 8-bit-or-narrower passes; 4..8 = at most that many bits per pass).  The
- * digit width changes speed only, never the sorted result. */
+ * and the radix sort's digit width (0 = automatic: at most 8 bits per pass;
+ * 4..8 = at most that many bits per pass; the pass count then follows on the
+ * device from the frame's depth range, see gs_sort).  The digit width changes
+ * speed only, never the sorted result. */
 typedef struct gs_raster_cfg {
     int32_t tile;
     int32_t mode;
