@@ -206,8 +206,10 @@ struct KeyWriter {
     }
 };
 
-template <bool kMulti>
-__global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
+// One instantiation per tile mode, so each mode's kernel holds only its own
+// tile-set code (and its registers are allocated for that code alone).
+template <bool kMulti, int kMode>
+__global__ void __launch_bounds__(kScanThreads, 4) emit_kernel(const EmitArgs A) {
     pdl_begin();
     __shared__ long long s_warp[32];
     if (A.status[2] & GS_FLAG_CAPACITY) return;  // keys do not fit: emit nothing
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
         const int64_t i = block0 + (int64_t)r * kScanThreads + threadIdx.x;
         cnt[r] = i < A.n ? A.counts[i] : 0;
     }
-    const bool three = A.mode == GS_MODE_3SIGMA;
+    constexpr bool three = kMode == GS_MODE_3SIGMA;
     float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
     int rad = 0;
     if (cnt[0] > 0) {
@@ -276,12 +278,12 @@ __global__ void __launch_bounds__(kScanThreads) emit_kernel(const EmitArgs A) {
                 Snug S;
                 if (snugbox(E, grid, S)) {
                     auto put = [&](int tx, int ty) { W.put((uint32_t)(ty * grid.gx + tx)); };
-                    if (A.mode == GS_MODE_SNUGBOX) {
+                    if (kMode == GS_MODE_SNUGBOX) {
                         for (int ty = S.R.y0; ty <= S.R.y1; ++ty)
                             for (int tx = S.R.x0; tx <= S.R.x1; ++tx) W.put((uint32_t)(ty * grid.gx + tx));
-                    } else if (A.mode == GS_MODE_TBC) {
+                    } else if (kMode == GS_MODE_TBC) {
                         tbc_tiles(E, S, grid, put);
-                    } else if (A.mode == GS_MODE_PIXEL) {
+                    } else if (kMode == GS_MODE_PIXEL) {
                         pixel_tiles(E, S, grid, put);
                     } else {
                         accutile_sweep(E, S, grid, W);
@@ -327,8 +329,17 @@ gs_status launch_intersect(gs_context* ctx, const gs_raster_cfg* cfg, const Fram
         A.grid = Grid{(float)v.tile, v.gx, v.gy, v.width, v.height};
         A.table = v.table;
         A.cam_stride = v.cam_stride;
-        if (v.table) (void)launch_pdl(ctx->stream, emit_kernel<true>, dim3((unsigned)nb), dim3(kScanThreads), 0, A);
-        else (void)launch_pdl(ctx->stream, emit_kernel<false>, dim3((unsigned)nb), dim3(kScanThreads), 0, A);
+#define GS_EMIT(M_)                                                                                          \
+    (v.table ? launch_pdl(ctx->stream, emit_kernel<true, M_>, dim3((unsigned)nb), dim3(kScanThreads), 0, A)     \
+             : launch_pdl(ctx->stream, emit_kernel<false, M_>, dim3((unsigned)nb), dim3(kScanThreads), 0, A))
+        switch (cfg->mode) {
+            case GS_MODE_3SIGMA: (void)GS_EMIT(GS_MODE_3SIGMA); break;
+            case GS_MODE_SNUGBOX: (void)GS_EMIT(GS_MODE_SNUGBOX); break;
+            case GS_MODE_TBC: (void)GS_EMIT(GS_MODE_TBC); break;
+            case GS_MODE_PIXEL: (void)GS_EMIT(GS_MODE_PIXEL); break;
+            default: (void)GS_EMIT(GS_MODE_ACCUTILE); break;
+        }
+#undef GS_EMIT
         ctx->launches += 1;
     }
     return check_launch(ctx, "intersect");
