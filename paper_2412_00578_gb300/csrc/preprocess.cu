@@ -72,6 +72,7 @@ __device__ __forceinline__ void sh_basis16(float x, float y, float z, float Y[16
 // Gaussian i seen by camera C (grid g); writes slot o of the outputs.
 // Returns the depth bits of a Gaussian given tiles, else 0 (a counted
 // depth is above the near plane, so its bits are never 0).
+template <int kMode>
 __device__ __forceinline__ uint32_t preprocess_one(const PreArgs& A, const CamK& C, const Grid& grid, int64_t i,
                                                    int64_t o) {
     int count = 0;
@@ -195,7 +196,7 @@ __device__ __forceinline__ uint32_t preprocess_one(const PreArgs& A, const CamK&
                     const float rad = ceilf(3.0f * sqrtf(l1));
                     const int radius = (rad >= 0.0f && rad < 1073741824.0f) ? (int)rad : (1 << 30);
                     const Ellipse E{u, v, a, b, c, t};
-                    count = tile_count(A.mode, E, radius, grid);
+                    count = tile_count(kMode, E, radius, grid);  // kMode is a constant: one mode's code
                     if (count > 0) {
                         // SH colour, read only for Gaussians that touch a tile
                         const float d0 = mx - C.campos[0], d1 = my - C.campos[1], d2 = mz - C.campos[2];
@@ -242,15 +243,18 @@ __device__ __forceinline__ void record_depth_range(uint2* out, uint32_t db) {
         out[(int64_t)blockIdx.x * (kPreThreads / 32) + (threadIdx.x >> 5)] = make_uint2(lo_n, hi);
 }
 
+// One instantiation per tile mode, so each kernel holds only its mode's tile count.
+template <int kMode>
 __global__ void __launch_bounds__(kPreThreads, 4) preprocess_kernel(const PreArgs A) {
     pdl_begin();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t db = i < A.ncap ? preprocess_one(A, A.cam, A.grid, i, i) : 0u;
+    const uint32_t db = i < A.ncap ? preprocess_one<kMode>(A, A.cam, A.grid, i, i) : 0u;
     record_depth_range(A.warp_range, db);
 }
 
 // Multi-view: block b handles Gaussian chunk b / V for camera b % V, so the
 // cameras of one chunk run back to back and re-read its parameters from L2.
+template <int kMode>
 __global__ void __launch_bounds__(kPreThreads, 4) preprocess_multiview_kernel(const PreArgs A) {
     const int cam = (int)(blockIdx.x % (unsigned)A.num_cams);
     const int64_t i = (int64_t)(blockIdx.x / (unsigned)A.num_cams) * blockDim.x + threadIdx.x;
@@ -258,7 +262,7 @@ __global__ void __launch_bounds__(kPreThreads, 4) preprocess_multiview_kernel(co
     if (i < A.ncap) {
         const CamRec& R = A.table[cam];
         const Grid g{A.grid.T, R.gx, R.gy, R.width, R.height};
-        db = preprocess_one(A, R.k, g, i, (int64_t)cam * A.ncap + i);
+        db = preprocess_one<kMode>(A, R.k, g, i, (int64_t)cam * A.ncap + i);
     }
     record_depth_range(A.warp_range, db);
 }
@@ -302,13 +306,27 @@ gs_status launch_preprocess(gs_context* ctx, const gs_scene* s, const gs_camera*
         A.ncap = v.cam_stride;
         if (A.ncap == 0 || v.num_cams == 0) return GS_OK;
         const int64_t blocks = (A.ncap + threads - 1) / threads * v.num_cams;
-        preprocess_multiview_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(A);
+        switch (cfg->mode) {
+            case GS_MODE_3SIGMA: preprocess_multiview_kernel<GS_MODE_3SIGMA><<<(unsigned)blocks, threads, 0, ctx->stream>>>(A); break;
+            case GS_MODE_SNUGBOX: preprocess_multiview_kernel<GS_MODE_SNUGBOX><<<(unsigned)blocks, threads, 0, ctx->stream>>>(A); break;
+            case GS_MODE_TBC: preprocess_multiview_kernel<GS_MODE_TBC><<<(unsigned)blocks, threads, 0, ctx->stream>>>(A); break;
+            case GS_MODE_PIXEL: preprocess_multiview_kernel<GS_MODE_PIXEL><<<(unsigned)blocks, threads, 0, ctx->stream>>>(A); break;
+            default: preprocess_multiview_kernel<GS_MODE_ACCUTILE><<<(unsigned)blocks, threads, 0, ctx->stream>>>(A); break;
+        }
         ctx->launches += 1;
         return check_launch(ctx, "preprocess_multiview");
     }
     if (v.ncap == 0) return GS_OK;
     const int64_t blocks = (v.ncap + threads - 1) / threads;
-    (void)launch_pdl(ctx->stream, preprocess_kernel, dim3((unsigned)blocks), dim3(threads), 0, A);
+#define GS_PRE(M_) (void)launch_pdl(ctx->stream, preprocess_kernel<M_>, dim3((unsigned)blocks), dim3(threads), 0, A)
+    switch (cfg->mode) {
+        case GS_MODE_3SIGMA: GS_PRE(GS_MODE_3SIGMA); break;
+        case GS_MODE_SNUGBOX: GS_PRE(GS_MODE_SNUGBOX); break;
+        case GS_MODE_TBC: GS_PRE(GS_MODE_TBC); break;
+        case GS_MODE_PIXEL: GS_PRE(GS_MODE_PIXEL); break;
+        default: GS_PRE(GS_MODE_ACCUTILE); break;
+    }
+#undef GS_PRE
     ctx->launches += 1;
     return check_launch(ctx, "preprocess");
 }
