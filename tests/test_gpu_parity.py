@@ -394,6 +394,29 @@ def test_outdoor_pruned_300k(raster, outdoor):
     assert np.abs(out.image.cpu().numpy().astype(np.float64) - ref["image"]).max() <= IMG_TOL
 
 
+def test_outdoor_10m_1920x1080_forward(raster):
+    """A 10M-Gaussian scene of the same recipe at 1920x1080 (8,160 tiles,
+    40,000 preprocess warps, over 2,400 scan blocks): the gs_forward chain with
+    its device-chosen sort plan, against the oracle's keys, ranges and image."""
+    scene, cam = synth.outdoor_workload(n=10_000_000, seed=4, width=1920, height=1080)
+    r = raster.Rasterizer("cuda:0")
+    ref = oracle.render(scene, cam, 16, 2, prec64=False, omp=True)
+    K = ref["num_keys"]
+    frame = raster.Frame(scene.n, cam.width, cam.height, 16, K + 1000, "cuda:0")
+    cfg = raster.cfg_struct(16, 2)
+    r.gs_forward(scene.to("cuda:0"), cam, cfg, frame)
+    k, flags = r.gs_read_status(frame)
+    assert k == K and flags == 0
+    keys = ref["keys"]
+    tiles = -(-cam.width // 16) * -(-cam.height // 16)
+    assert r.gs_read_sort_plan(cfg, frame) == expected_sort_plan(keys, tiles, 0)
+    assert np.array_equal(frame.keys[:K].cpu().numpy().view(np.uint64), keys)
+    assert np.array_equal(frame.vals[:K].cpu().numpy().view(np.uint32), ref["vals"])
+    assert np.array_equal(frame.tile_ranges().cpu().numpy().view(np.uint32), ref["ranges"])
+    assert np.abs(frame.image.cpu().numpy().astype(np.float64) - ref["image"]).max() <= IMG_TOL
+    print(f"outdoor 10M 1920x1080: K={K}, plan {r.gs_read_sort_plan(cfg, frame)}")
+
+
 # ---------------------------------------------------------------- gs_forward
 def run_forward(raster, rast, scene, cam, mode, tile, bg=(0.0, 0.0, 0.0), key_capacity=None, n_capacity=None,
                 sort_digit_bits=0):
