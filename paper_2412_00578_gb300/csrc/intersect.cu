@@ -211,7 +211,7 @@ struct KeyWriter {
 template <bool kMulti, int kMode>
 __global__ void __launch_bounds__(kScanThreads, 4) emit_kernel(const EmitArgs A) {
     pdl_begin();
-    __shared__ long long s_warp[32];
+    __shared__ int s_tot[kScanItems][kScanThreads / 32];
     if (A.status[2] & GS_FLAG_CAPACITY) return;  // keys do not fit: emit nothing
     if (kMulti && A.status[3]) return;           // cameras do not fit the batch frame
     // The block's 1024 slots are taken in 4 rounds of 256 consecutive ones
@@ -220,14 +220,47 @@ __global__ void __launch_bounds__(kScanThreads, 4) emit_kernel(const EmitArgs A)
     // Gaussian (single view) or a (camera, Gaussian) pair, camera-major.
     // Software pipeline: the four rounds' counts are loaded up front, and
     // while a round is processed the next round's 2D state is already in
-    // flight, so the rounds do not wait on memory one after another.
-    long long carry = A.partials[blockIdx.x];
+    // flight, so the rounds do not wait on memory one after another.  The
+    // slots' offsets come from one scan of all four rounds before the first
+    // (lane prefixes by warp shuffles, warp totals exchanged once), so the
+    // rounds themselves need no barrier.  Offsets within the block fit 32
+    // bits: the emit runs only when K <= key_capacity < 2^30.
+    const long long carry = A.partials[blockIdx.x];
     const int64_t block0 = (int64_t)blockIdx.x * kScanBlock;
     int cnt[kScanItems];
 #pragma unroll
     for (int r = 0; r < kScanItems; ++r) {
         const int64_t i = block0 + (int64_t)r * kScanThreads + threadIdx.x;
         cnt[r] = i < A.n ? A.counts[i] : 0;
+    }
+    int excl[kScanItems];  // slot offset within the block
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int r = 0; r < kScanItems; ++r) {
+            int inc = cnt[r];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            excl[r] = inc - cnt[r];
+            if (lane == 31) s_tot[r][warp] = inc;
+        }
+        __syncthreads();
+        int before = 0;  // the block's earlier rounds
+#pragma unroll
+        for (int r = 0; r < kScanItems; ++r) {
+            int wpre = 0, rtot = 0;
+#pragma unroll
+            for (int w = 0; w < kScanThreads / 32; ++w) {
+                const int t = s_tot[r][w];
+                rtot += t;
+                if (w < warp) wpre += t;
+            }
+            excl[r] += before + wpre;
+            before += rtot;
+        }
     }
     constexpr bool three = kMode == GS_MODE_3SIGMA;
     float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
@@ -250,10 +283,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) emit_kernel(const EmitArgs A)
             if (three) nrad = __float_as_int(A.p2[in].w);
             else n1 = A.p1[in];
         }
-        long long total;
-        const long long off = carry + block_excl_scan(c, s_warp, &total);
-        __syncthreads();  // s_warp is reused by the next round's scan
-        carry += total;
+        const long long off = carry + excl[r];
         if (c > 0) {
             Grid grid = A.grid;
             uint32_t tile0 = 0, id = (uint32_t)i;
