@@ -193,7 +193,7 @@ __device__ __forceinline__ void st_relaxed_gpu(uint32_t* p, uint32_t v) {
 }
 
 
-// ---------------------------------------------------------------- block scan
+// ---------------------------------------------------------------- warp scan
 __device__ __forceinline__ long long warp_incl_scan(long long v, int lane) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -201,24 +201,6 @@ __device__ __forceinline__ long long warp_incl_scan(long long v, int lane) {
         if (lane >= o) v += y;
     }
     return v;
-}
-
-// Exclusive scan across a 256-thread block; returns the thread's exclusive
-// prefix and writes the block total to *total.
-__device__ __forceinline__ long long block_excl_scan(long long v, long long* s_warp, long long* total) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long inc = warp_incl_scan(v, lane);
-    if (lane == 31) s_warp[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        long long w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
-        w = warp_incl_scan(w, lane);
-        if (lane < (int)(blockDim.x >> 5)) s_warp[lane] = w;
-    }
-    __syncthreads();
-    const long long before = warp > 0 ? s_warp[warp - 1] : 0;
-    *total = s_warp[(blockDim.x >> 5) - 1];
-    return before + inc - v;
 }
 
 // ---------------------------------------------------------------- programmatic dependent launch
