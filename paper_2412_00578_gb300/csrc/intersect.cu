@@ -17,21 +17,6 @@
 namespace gs {
 namespace {
 
-// Maximum of both words of a uint2 over the block (result in thread 0).
-__device__ __forceinline__ uint2 block_max2(uint2 v, uint2* s_warp) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v.x = __reduce_max_sync(0xffffffffu, v.x);
-    v.y = __reduce_max_sync(0xffffffffu, v.y);
-    if (lane == 0) s_warp[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        const bool w = lane < (int)(blockDim.x >> 5);
-        v.x = __reduce_max_sync(0xffffffffu, w ? s_warp[lane].x : 0u);
-        v.y = __reduce_max_sync(0xffffffffu, w ? s_warp[lane].y : 0u);
-    }
-    return v;
-}
-
 // Each block sums its kScanBlock counts and reduces its share of the
 // preprocess's per-warp depth ranges (an even split of the n_warps slots
 // over the blocks, independent of which Gaussians a warp held); one barrier
@@ -92,60 +77,57 @@ __global__ void __launch_bounds__(1024) scan_top_kernel(long long* __restrict__ 
     // a fused chain's sort control words (histograms, tickets) start at zero
     if (sort_ctl)
         for (int i = threadIdx.x; i < kSortCtlWords; i += blockDim.x) sort_ctl[i] = 0u;
-    __shared__ long long s_warp[32];
+    // Thread t takes a contiguous run of the partials: one pass sums its run
+    // and reduces the matching depth ranges, one block scan of the sums and
+    // one reduction of the ranges (sharing two barriers) give every run its
+    // offset, and a second pass writes the offsets.
+    __shared__ long long s_sum[32];
     __shared__ uint2 s_range[32];
-    __shared__ long long s_carry;
     __shared__ long long s_base;
-    // the frame's depth-bit range, from the scan blocks' shares
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t per = (nblocks + blockDim.x - 1) / blockDim.x;
+    const int64_t b_lo = min((int64_t)threadIdx.x * per, nblocks), b_hi = min(b_lo + per, nblocks);
+    long long sum = 0;
     uint2 r = make_uint2(0u, 0u);
-    if (block_range) {
-        // four loads in flight per thread
-        for (int64_t b0 = threadIdx.x; b0 < nblocks; b0 += 4 * (int64_t)blockDim.x) {
-            uint2 x[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t b = b0 + (int64_t)u * blockDim.x;
-                x[u] = b < nblocks ? block_range[b] : make_uint2(0u, 0u);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                r.x = max(r.x, x[u].x);
-                r.y = max(r.y, x[u].y);
-            }
+    for (int64_t b = b_lo; b < b_hi; ++b) {
+        sum += partials[b];
+        if (block_range) {
+            const uint2 x = block_range[b];
+            r.x = max(r.x, x.x);
+            r.y = max(r.y, x.y);
         }
     }
-    r = block_max2(r, s_range);
-    if (threadIdx.x == 0) {
-        s_carry = 0;
-        status[kStatusDepthLoN] = r.x;
-        status[kStatusDepthHi] = r.y;
-        // A fused call whose sort plan starts from buffer 1 has the emit write
-        // there: buffer 1 is buffer 0 displaced by the key capacity (keys and
-        // values alike), so every block offset starts at kcap.
-        const SortPlan P = sort_plan_of(r.x, r.y, tile_bits, dmax, true);
-        s_base = (fused && P.start) ? (long long)kcap : 0ll;
+    const long long inc = warp_incl_scan(sum, lane);
+    r.x = __reduce_max_sync(0xffffffffu, r.x);
+    r.y = __reduce_max_sync(0xffffffffu, r.y);
+    if (lane == 31) s_sum[warp] = inc;
+    if (lane == 0) s_range[warp] = r;
+    __syncthreads();
+    if (warp == 0) {
+        const bool w = lane < (int)(blockDim.x >> 5);
+        const long long ws = warp_incl_scan(w ? s_sum[lane] : 0ll, lane);
+        uint2 m = w ? s_range[lane] : make_uint2(0u, 0u);
+        m.x = __reduce_max_sync(0xffffffffu, m.x);
+        m.y = __reduce_max_sync(0xffffffffu, m.y);
+        if (w) s_sum[lane] = ws;
+        if (lane == 0) {
+            status[kStatusDepthLoN] = m.x;
+            status[kStatusDepthHi] = m.y;
+            // A fused call whose sort plan starts from buffer 1 has the emit
+            // write there: buffer 1 is buffer 0 displaced by the key capacity
+            // (keys and values alike), so every block offset starts at kcap.
+            const SortPlan P = sort_plan_of(m.x, m.y, tile_bits, dmax, true);
+            s_base = (fused && P.start) ? (long long)kcap : 0ll;
+        }
     }
     __syncthreads();
-    for (int64_t b0 = 0; b0 < nblocks; b0 += blockDim.x) {
-        const int64_t b = b0 + threadIdx.x;
-        const long long v = b < nblocks ? partials[b] : 0;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const long long inc = warp_incl_scan(v, lane);
-        if (lane == 31) s_warp[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            long long w = s_warp[lane];
-            w = warp_incl_scan(w, lane);
-            s_warp[lane] = w;
-        }
-        __syncthreads();
-        const long long excl = (warp > 0 ? s_warp[warp - 1] : 0) + inc - v;
-        const long long carry = s_carry;
-        if (b < nblocks) partials[b] = s_base + carry + excl;
-        __syncthreads();
-        if (threadIdx.x == 0) s_carry = carry + s_warp[31];
-        __syncthreads();
+    long long run = s_base + (warp > 0 ? s_sum[warp - 1] : 0ll) + (inc - sum);
+    for (int64_t b = b_lo; b < b_hi; ++b) {
+        const long long v = partials[b];
+        partials[b] = run;
+        run += v;
     }
+    const long long s_carry = s_sum[(blockDim.x >> 5) - 1];  // the key total K
     if (threadIdx.x == 0) {
         const long long K = s_carry;
         // words 0..2 (and 3 for a single camera; a batch's set-up kernel has
