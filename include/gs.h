@@ -391,6 +391,17 @@ gs_status gs_read_culled(gs_context* ctx, const gs_frame* frame, int64_t* culled
 gs_status gs_read_sort_plan(gs_context* ctx, const gs_raster_cfg* cfg, const gs_frame* frame, int32_t* passes,
                             int32_t* digit_bits, int32_t* depth_bits);
 
+/* The same plan as a pure host function of its inputs (no context, no
+ * device): a frame of `tiles` tiles whose keys' depth bits lie in
+ * [least, greatest] (least > greatest: no range recorded, all 32 depth bits
+ * kept), at most `sort_digit_bits` bits per digit (0 = 8), for gs_forward
+ * (fused != 0) or a stand-alone gs_sort (even pass count).  Outputs (host,
+ * nullable): the pass count, bits per digit, depth bits kept, and the buffer
+ * (0 or 1) the emit writes and the first pass reads.  GS_ERR_INVALID for
+ * tiles < 1 or a digit width outside {0, 4..8}. */
+gs_status gs_sort_plan_for(int64_t tiles, uint32_t least, uint32_t greatest, int32_t sort_digit_bits, int32_t fused,
+                           int32_t* passes, int32_t* digit_bits, int32_t* depth_bits, int32_t* start_buffer);
+
 /* Failure detection of the sort's bounded waits.  Each decoupled look-back
  * wait of gs_sort gives up after max_polls polls (0 = the default, 4,194,304,
  * far beyond any wait of a correct run) and then sets GS_FLAG_TIMEOUT.  If

@@ -382,6 +382,20 @@ gs_status gs_read_sort_plan(gs_context* ctx, const gs_raster_cfg* cfg, const gs_
     return GS_OK;
 }
 
+gs_status gs_sort_plan_for(int64_t tiles, uint32_t least, uint32_t greatest, int32_t sort_digit_bits, int32_t fused,
+                           int32_t* passes, int32_t* digit_bits, int32_t* depth_bits, int32_t* start_buffer) {
+    if (tiles < 1 || (sort_digit_bits != 0 && (sort_digit_bits < 4 || sort_digit_bits > 8))) return GS_ERR_INVALID;
+    // the status-word form: complement of the least bits, greatest bits; both 0 = none recorded
+    const uint32_t lo_n = least > greatest ? 0u : ~least;
+    const uint32_t hi = least > greatest ? 0u : greatest;
+    const SortPlan P = sort_plan_of(lo_n, hi, sort_tile_bits(tiles), sort_digit_max(sort_digit_bits), fused != 0);
+    if (passes) *passes = P.passes;
+    if (digit_bits) *digit_bits = P.dbits;
+    if (depth_bits) *depth_bits = P.w;
+    if (start_buffer) *start_buffer = P.start;
+    return GS_OK;
+}
+
 gs_status gs_read_status(gs_context* ctx, const gs_frame* frame, int64_t* num_keys, uint32_t* flags) {
     gs_status st = enter(ctx);
     if (st) return st;

@@ -74,7 +74,7 @@ EXPORTS = ["gs_create", "gs_destroy", "gs_set_stream", "gs_last_error", "gs_laun
            "gs_preprocess", "gs_intersect", "gs_sort", "gs_tile_ranges", "gs_render", "gs_render_stats",
            "gs_forward", "gs_read_status", "gs_backward_work_bytes", "gs_render_backward", "gs_intersect_noalloc",
            "gs_batch_sizes", "gs_forward_batch", "gs_batch_status", "gs_read_culled", "gs_set_sort_wait",
-           "gs_pup_work_bytes", "gs_pup_accumulate", "gs_pup_score", "gs_read_sort_plan"]
+           "gs_pup_work_bytes", "gs_pup_accumulate", "gs_pup_score", "gs_read_sort_plan", "gs_sort_plan_for"]
 
 _lib = None
 
@@ -107,6 +107,8 @@ def load(path=None) -> ctypes.CDLL:
     L.gs_read_status.argtypes = [P, POINTER(GsFrame), POINTER(c_int64), POINTER(c_uint32)]
     L.gs_read_sort_plan.argtypes = [P, POINTER(GsRasterCfg), POINTER(GsFrame), POINTER(c_int32), POINTER(c_int32),
                                     POINTER(c_int32)]
+    L.gs_sort_plan_for.argtypes = [c_int64, c_uint32, c_uint32, c_int32, c_int32, POINTER(c_int32), POINTER(c_int32),
+                                   POINTER(c_int32), POINTER(c_int32)]
     L.gs_render_stats.argtypes = [P, POINTER(GsCamera), POINTER(GsRasterCfg), POINTER(GsFrame),
                                   POINTER(ctypes.c_uint64), POINTER(ctypes.c_uint64), POINTER(ctypes.c_uint64)]
     L.gs_backward_work_bytes.argtypes = [c_int64]
@@ -438,6 +440,17 @@ class Renderer:
 
 def backward_work_bytes(n: int) -> int:
     return int(load().gs_backward_work_bytes(int(n)))
+
+
+def sort_plan_for(tiles: int, least: int, greatest: int, sort_digit_bits: int = 0, fused: bool = True):
+    """(passes, digit_bits, depth_bits, start_buffer) of the sort plan for keys
+    whose depth bits lie in [least, greatest] (least > greatest: none recorded)."""
+    out = [c_int32(0) for _ in range(4)]
+    st = load().gs_sort_plan_for(int(tiles), int(least), int(greatest), int(sort_digit_bits), int(bool(fused)),
+                                 *[ctypes.byref(o) for o in out])
+    if st:
+        raise GsError(st, f"gs_sort_plan_for(tiles={tiles}, digits={sort_digit_bits})")
+    return tuple(int(o.value) for o in out)
 
 
 def pup_work_bytes(n: int) -> int:
