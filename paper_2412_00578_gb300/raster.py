@@ -584,7 +584,7 @@ class BatchFrame:
         self.image = e(sz.image, torch.float32, 4)
         self.final_T = e(sz.final_T, torch.float32, 4)
         self.last = e(sz.last, torch.int32, 4)
-        self.scratch = e(sz.scratch, torch.uint8, 1)
+        self.scratch = torch.zeros(max(sz.scratch, 1), dtype=torch.uint8, device=device)
         self.cams_dev = torch.empty(max_cams * CAMERA_BYTES, dtype=torch.uint8, device=device)
         f = GsBatchFrame()
         f.n_capacity, f.key_capacity = n, key_capacity
