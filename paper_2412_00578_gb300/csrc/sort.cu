@@ -6,13 +6,14 @@
 //               bin per block) and clears the first look-back table; the
 //               last block to finish picks each pass's ranking method from
 //               the finished histogram (below).
-//   sort_pass   one launch per digit.  Each block takes a 4096-key partition
-//               by atomic ticket (so partitions are processed in launch
-//               order and every predecessor is already resident), ranks its
-//               keys by digit stably (the lanes of a warp holding equal
-//               digits find each other, then per-warp counters), publishes
-//               its per-digit counts, and resolves its global
-//               offsets by decoupled look-back over its predecessors'
+//   sort_pass   one launch per digit, at most two CTAs per SM that stay
+//               resident: each takes 4096-key partitions by atomic ticket
+//               until none is left (so partitions are processed in ticket
+//               order and every predecessor is held by a running or finished
+//               CTA), ranks a partition's keys by digit stably (the lanes of
+//               a warp holding equal digits find each other, then per-warp
+//               counters), publishes its per-digit counts, and resolves its
+//               global offsets by decoupled look-back over its predecessors'
 //               published counts.  Keys are staged in shared memory in digit
 //               order so each digit's run is written to HBM contiguously.
 //               Every wait on a predecessor is bounded; when the bound is
@@ -25,11 +26,12 @@
 // image (tile << w) | (depth bits - dmin), which is strictly increasing in
 // the key over the frame's keys, so sorting the images sorts the keys.  The
 // first pass turns each key it reads into its image, the passes in between
-// move images, and the last pass writes each key back in full.  The plan (pass count P, digit width) is a
-// function of the status words, evaluated alike by every block of every
-// sort kernel (sort_plan_of); the host launches the most passes any plan of
-// the frame can need and the launches past P return at once.  The passes
-// alternate between buffers 0 and 1 and the last one writes buffer 0: a
+// move images, and the last pass writes each key back in full.  The plan
+// (pass count P, digit width) is a function of the status words, evaluated
+// alike by every block of every sort kernel (sort_plan_of); the host launches
+// the most passes any plan of the frame can need and the launches past P
+// return at once.  The passes alternate between buffers 0 and 1 and the last
+// one writes buffer 0: a
 // stand-alone gs_sort (whose keys gs_intersect left in buffer 0) rounds P up
 // to even, while gs_forward's chain lets the emit write buffer 1 when P is
 // odd (the scan's offsets say where).
