@@ -41,8 +41,9 @@
 // into its digit's word costs more the more lanes share a digit.  Both give
 // the same peer masks, so the ranks (and the sort) do not depend on the
 // choice.  A pass whose digits are spread out (collision probability
-// sum_d (n_d / K)^2 at most 1/32) ranks by atomicOr, a concentrated one (the
-// top depth byte, the top tile bits) by match.
+// sum_d (n_d / K)^2 at most 1/8) ranks by atomicOr, a concentrated one (a
+// depth byte of a frame at nearly one depth, the top tile bits of a tile-heavy
+// digit) by match.
 #include <algorithm>
 
 #include "gs_common.cuh"
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const HistArgs A) {
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-        if (lane == 0) A.method[p] = (sq * 32.0 > kk) ? kRankMatch : 0u;
+        if (lane == 0) A.method[p] = (sq * 8.0 > kk) ? kRankMatch : 0u;
     }
 }
 
