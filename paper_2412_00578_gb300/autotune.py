@@ -24,8 +24,8 @@ CANDIDATES = [(t, d) for t in (8, 16, 32) for d in (0, 7, 6, 5, 4)]  # d = 0: 8-
 CACHE = Path(__file__).resolve().parent / "_build" / "autotune.json"
 
 
-def bucket_key(device, n, cams, mode) -> str:
-    name = torch.cuda.get_device_name(device).replace(" ", "_")
+def bucket_key(device_name: str, n, cams, mode) -> str:
+    name = device_name.replace(" ", "_")
     pixels = sum(c.width * c.height for c in cams)
     return f"{name}|n2^{max(0, round(math.log2(max(n, 1))))}|px2^{max(0, round(math.log2(max(pixels, 1))))}" \
            f"|v{len(cams)}|{mode}"
@@ -45,11 +45,16 @@ def _time(renderer, scene, cams, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def tune(scene, cams, device=None, mode="accutile", reps=5, cache_path: Path | None = CACHE, force=False):
-    """Returns {"tile", "sort_digit_bits", "ms", "timings"} for this batch."""
+def tune(scene, cams, device=None, mode="accutile", reps=5, cache_path: Path | None = CACHE, force=False,
+         timer=None, device_name: str | None = None):
+    """Returns {"tile", "sort_digit_bits", "ms", "timings", "cached"} for this
+    batch.  timer(tile, sort_digit_bits) -> ms replaces the CUDA-event timing
+    of a BatchRenderer (and device_name the device query) where given."""
     device = torch.device(device or "cuda")
     n = int(scene.means.shape[1])
-    key = bucket_key(device, n, cams, mode)
+    if device_name is None:
+        device_name = torch.cuda.get_device_name(device)
+    key = bucket_key(device_name, n, cams, mode)
     cache = {}
     if cache_path is not None and cache_path.exists():
         try:
@@ -58,12 +63,14 @@ def tune(scene, cams, device=None, mode="accutile", reps=5, cache_path: Path | N
             cache = {}
     if not force and key in cache:
         return dict(cache[key], cached=True)
-    timings = {}
-    for tile, d in CANDIDATES:
-        r = raster.BatchRenderer(device, tile=tile, mode=mode, sort_digit_bits=d)
-        timings[f"{tile}/{d or 8}"] = _time(r, scene, cams, reps)
-        del r
-        torch.cuda.empty_cache()
+    if timer is None:
+        def timer(tile, d):
+            r = raster.BatchRenderer(device, tile=tile, mode=mode, sort_digit_bits=d)
+            ms = _time(r, scene, cams, reps)
+            del r
+            torch.cuda.empty_cache()
+            return ms
+    timings = {f"{tile}/{d or 8}": float(timer(tile, d)) for tile, d in CANDIDATES}
     best = min(timings, key=timings.get)
     tile, d = (int(x) for x in best.split("/"))
     choice = {"tile": tile, "sort_digit_bits": 0 if d == 8 else d, "ms": timings[best], "timings": timings}
