@@ -53,6 +53,14 @@ class Schedule:
     def at(self, it: int) -> int:
         return int(round(it * self.scale))
 
+    def events(self, total: int, prune: bool = True):
+        """Iterations of the Soft Prunes, the opacity resets and the Hard
+        Prunes of a run of `total` iterations (scaled counts)."""
+        soft = {self.at(x) for x in self.soft_at} if prune else set()
+        resets = set(range(self.at(self.reset_every), self.at(self.densify_until), max(self.at(self.reset_every), 1)))
+        hard = set(range(self.at(self.hard_from), total + 1, max(self.at(self.hard_every), 1))) if prune else set()
+        return soft, resets, hard
+
 
 class Model:
     """Raw (pre-activation) Gaussian parameters and their Adam optimiser."""
@@ -274,9 +282,7 @@ def fit(task: Task, device, sch: Schedule, prune: bool = True, score: str = "eff
     seen = torch.zeros(model.n, device=dev)
     events = []
     order = torch.randperm(len(task.train), generator=gen).tolist()
-    soft = {sch.at(x) for x in sch.soft_at}
-    resets = set(range(sch.at(sch.reset_every), sch.at(sch.densify_until), max(sch.at(sch.reset_every), 1)))
-    hard = set(range(sch.at(sch.hard_from), total + 1, max(sch.at(sch.hard_every), 1))) if prune else set()
+    soft, resets, hard = sch.events(total, prune)
     lr0 = model.opt.param_groups[0]["lr"]
     t0 = time.perf_counter()
     for it in range(1, total + 1):
