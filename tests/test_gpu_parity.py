@@ -235,6 +235,20 @@ def test_one_depth_for_the_whole_frame(raster, rast):
     assert np.all(gpu["vals"][1:][same] > gpu["vals"][:-1][same])
 
 
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_one_depth_forward_keeps_no_depth_bits(raster, rast, tile):
+    """The same one-depth frame through gs_forward: the plan keeps no depth
+    bits (the tile bits alone decide the order, in two passes or more), and
+    the pairs, ranges and image are the oracle's."""
+    scene = synth.uniform_box_scene(30000, seed=61, half=2.0, log_scale_mu=-3.5, log_scale_sd=0.6)
+    scene.means[2] = 0.0
+    cam = synth.pinhole(320, 240, 60.0, np.eye(3), np.array([0.0, 0.0, 5.0]))
+    frame, K = check_forward(raster, rast, scene, cam, 2, tile)
+    passes, dbits, w = rast.gs_read_sort_plan(raster.cfg_struct(tile, 2), frame)
+    tiles = -(-cam.width // tile) * -(-cam.height // tile)
+    assert w == 0 and passes * dbits >= max(tiles - 1, 0).bit_length() and passes >= 2
+
+
 @pytest.mark.parametrize("digits", [6, 5, 4])
 def test_digit_widths_agree(raster, rast, digits):
     """Narrower radix digits (more passes) give the same sorted pairs, bit for
