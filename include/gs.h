@@ -166,7 +166,9 @@ gs_status gs_frame_sizes(int64_t n_capacity, int32_t width, int32_t height, int3
  * projected mean and depth, Sigma3D = R S S^T R^T, Sigma2D = J W Sigma3D W^T J^T
  * (+0.3 I), its inverse (the conic), t = 2 log(255 sigma) (Sec. 4.1), the 3D-GS
  * radius, the SH colour, and the number of tiles touched in cfg->mode.
- * Writes frame->proj (for counted Gaussians) and frame->counts[0..n). */
+ * Writes frame->proj (for counted Gaussians) and frame->counts[0..n), and in
+ * frame->scratch the depth-bit range of the Gaussians given tiles, which
+ * gs_intersect records for the sort (see gs_sort). */
 gs_status gs_preprocess(gs_context* ctx, const gs_scene* scene, const gs_camera* cam, const gs_raster_cfg* cfg,
                         const gs_frame* frame);
 
