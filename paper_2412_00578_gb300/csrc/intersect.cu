@@ -193,7 +193,13 @@ struct KeyWriter {
 template <bool kMulti, int kMode>
 __global__ void __launch_bounds__(kScanThreads, 4) emit_kernel(const EmitArgs A) {
     pdl_begin();
-    __shared__ int s_tot[kScanItems][kScanThreads / 32];
+    constexpr bool kDefer = kMode == GS_MODE_ACCUTILE;
+    constexpr int kWarps = kScanThreads / 32;
+    __shared__ int s_tot[kScanItems][kWarps];
+    // AccuTile Gaussians that need the sweep (all but whole single lines),
+    // queued per warp as (slot in block, key offset in block) and swept
+    // together after the rounds
+    __shared__ int2 s_q[kDefer ? kWarps : 1][kDefer ? kScanBlock / kWarps : 1];
     if (A.status[2] & GS_FLAG_CAPACITY) return;  // keys do not fit: emit nothing
     if (kMulti && A.status[3]) return;           // cameras do not fit the batch frame
     // The block's 1024 slots are taken in 4 rounds of 256 consecutive ones
@@ -215,9 +221,9 @@ __global__ void __launch_bounds__(kScanThreads, 4) emit_kernel(const EmitArgs A)
         const int64_t i = block0 + (int64_t)r * kScanThreads + threadIdx.x;
         cnt[r] = i < A.n ? A.counts[i] : 0;
     }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int excl[kScanItems];  // slot offset within the block
     {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
         for (int r = 0; r < kScanItems; ++r) {
             int inc = cnt[r];
@@ -244,6 +250,24 @@ __global__ void __launch_bounds__(kScanThreads, 4) emit_kernel(const EmitArgs A)
             before += rtot;
         }
     }
+    // grid, first global tile and Gaussian id of slot i (its camera's, in a
+    // multi-view batch)
+    auto slot_frame = [&](int64_t i, Grid& grid, uint32_t& tile0, uint32_t& id) {
+        grid = A.grid;
+        tile0 = 0;
+        id = (uint32_t)i;
+        if (kMulti) {
+            const int64_t cam = i / A.cam_stride;
+            const CamRec& R = A.table[cam];
+            grid.gx = R.gx;
+            grid.gy = R.gy;
+            grid.W = R.width;
+            grid.H = R.height;
+            tile0 = (uint32_t)R.tile_offset;
+            id = (uint32_t)(i - cam * A.cam_stride);
+        }
+    };
+    int qn = 0;  // queued slots of this warp (AccuTile)
     constexpr bool three = kMode == GS_MODE_3SIGMA;
     float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
     int rad = 0;
@@ -266,19 +290,11 @@ __global__ void __launch_bounds__(kScanThreads, 4) emit_kernel(const EmitArgs A)
             else n1 = A.p1[in];
         }
         const long long off = carry + excl[r];
+        bool defer = false;
         if (c > 0) {
-            Grid grid = A.grid;
-            uint32_t tile0 = 0, id = (uint32_t)i;
-            if (kMulti) {
-                const int64_t cam = i / A.cam_stride;
-                const CamRec& R = A.table[cam];
-                grid.gx = R.gx;
-                grid.gy = R.gy;
-                grid.W = R.width;
-                grid.H = R.height;
-                tile0 = (uint32_t)R.tile_offset;
-                id = (uint32_t)(i - cam * A.cam_stride);
-            }
+            Grid grid;
+            uint32_t tile0, id;
+            slot_frame(i, grid, tile0, id);
             KeyWriter W{A.keys, A.vals, off, off + c, __float_as_uint(q0.w), id, grid.gx, tile0};
             if (three) {
                 Rect R;
@@ -298,14 +314,42 @@ __global__ void __launch_bounds__(kScanThreads, 4) emit_kernel(const EmitArgs A)
                     } else if (kMode == GS_MODE_PIXEL) {
                         pixel_tiles(E, S, grid, put);
                     } else {
-                        accutile_sweep(E, S, grid, W);
+                        int k, j0, j1;
+                        bool rows;
+                        if (accutile_whole_line(S, grid, k, j0, j1, rows)) W(k, j0, j1, rows);
+                        else defer = true;
                     }
                 }
             }
         }
+        if (kDefer) {
+            const unsigned m = __ballot_sync(0xffffffffu, defer);
+            if (defer) s_q[warp][qn + __popc(m & ((1u << lane) - 1u))] = make_int2(r * kScanThreads + threadIdx.x, excl[r]);
+            qn += __popc(m);
+        }
         q0 = n0;
         q1 = n1;
         rad = nrad;
+    }
+    if (kDefer && qn > 0) {
+        // one lane per queued Gaussian: the warp runs the sweeps of all four
+        // rounds side by side instead of once per round
+        __syncwarp();
+        for (int b = 0; b < qn; b += 32) {
+            if (b + lane < qn) {
+                const int2 it = s_q[warp][b + lane];
+                const int64_t i = block0 + it.x;
+                const float4 a0 = A.p0[i], a1 = A.p1[i];
+                const long long off = carry + it.y;
+                Grid grid;
+                uint32_t tile0, id;
+                slot_frame(i, grid, tile0, id);
+                KeyWriter W{A.keys, A.vals, off, off + A.counts[i], __float_as_uint(a0.w), id, grid.gx, tile0};
+                const Ellipse E{a0.x, a0.y, a1.x, a1.y, a1.z, a1.w};
+                Snug S;
+                if (snugbox(E, grid, S)) accutile_sweep(E, S, grid, W);
+            }
+        }
     }
 }
 

@@ -157,6 +157,25 @@ __device__ __forceinline__ int accutile_sweep(const Ellipse& E, const Snug& S, c
     return cnt;
 }
 
+// The cases where accutile_sweep's result is its single line, whole: a
+// rectangle one tile line thick on its shorter side whose two boundaries both
+// lie outside the SnugBox span.  Neither boundary is then intersected, so the
+// line's extent is the SnugBox edges, which floor to exactly the rectangle's
+// span (the same products and clamps as in snugbox).  On true, (k, j0, j1,
+// rows) is the sweep's one emit call.
+__device__ __forceinline__ bool accutile_whole_line(const Snug& S, const Grid& g, int& k, int& j0, int& j1,
+                                                    bool& rows) {
+    rows = (S.R.y1 - S.R.y0) <= (S.R.x1 - S.R.x0);
+    k = rows ? S.R.y0 : S.R.x0;
+    if (k != (rows ? S.R.y1 : S.R.x1)) return false;
+    const float s_lo = rows ? S.y0 : S.x0;
+    const float s_hi = rows ? S.y1 : S.x1;
+    if ((float)k * g.T >= s_lo || (float)(k + 1) * g.T <= s_hi) return false;
+    j0 = rows ? S.R.x0 : S.R.y0;
+    j1 = rows ? S.R.x1 : S.R.y1;
+    return true;
+}
+
 struct NoEmit {
     __device__ __forceinline__ void operator()(int, int, int, bool) const {}
 };
@@ -311,6 +330,9 @@ __device__ __forceinline__ int tile_count(int mode, const Ellipse& E, int radius
     if (mode == GS_MODE_SNUGBOX) return (S.R.x1 - S.R.x0 + 1) * (S.R.y1 - S.R.y0 + 1);
     if (mode == GS_MODE_TBC) return tbc_tiles(E, S, g, NoPut{});
     if (mode == GS_MODE_PIXEL) return pixel_tiles(E, S, g, NoPut{});
+    int k, j0, j1;
+    bool rows;
+    if (accutile_whole_line(S, g, k, j0, j1, rows)) return j1 - j0 + 1;
     return accutile_sweep(E, S, g, NoEmit{});
 }
 
