@@ -193,12 +193,14 @@ struct KeyWriter {
 template <bool kMulti, int kMode>
 __global__ void __launch_bounds__(kScanThreads, 4) emit_kernel(const EmitArgs A) {
     pdl_begin();
-    constexpr bool kDefer = kMode == GS_MODE_ACCUTILE;
+    constexpr bool kDefer = kMode == GS_MODE_ACCUTILE || kMode == GS_MODE_TBC || kMode == GS_MODE_PIXEL;
     constexpr int kWarps = kScanThreads / 32;
     __shared__ int s_tot[kScanItems][kWarps];
-    // AccuTile Gaussians that need the sweep (all but whole single lines),
-    // queued per warp as (slot in block, key offset in block) and swept
-    // together after the rounds
+    // Gaussians whose tiles are not a whole rectangle known in advance
+    // (AccuTile: all but whole single lines; tile-based culling and
+    // pixel-exact tiles: those that keep fewer tiles than their candidate
+    // rectangle holds), queued per warp as (slot in block, key offset in
+    // block) and handled together after the rounds
     __shared__ int2 s_q[kDefer ? kWarps : 1][kDefer ? kScanBlock / kWarps : 1];
     if (A.status[2] & GS_FLAG_CAPACITY) return;  // keys do not fit: emit nothing
     if (kMulti && A.status[3]) return;           // cameras do not fit the batch frame
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) emit_kernel(const EmitArgs A)
             id = (uint32_t)(i - cam * A.cam_stride);
         }
     };
-    int qn = 0;  // queued slots of this warp (AccuTile)
+    int qn = 0;  // queued slots of this warp
     constexpr bool three = kMode == GS_MODE_3SIGMA;
     float4 q0 = make_float4(0.f, 0.f, 0.f, 0.f), q1 = q0;
     int rad = 0;
@@ -305,14 +307,25 @@ __global__ void __launch_bounds__(kScanThreads, 4) emit_kernel(const EmitArgs A)
                 const Ellipse E{q0.x, q0.y, q1.x, q1.y, q1.z, q1.w};
                 Snug S;
                 if (snugbox(E, grid, S)) {
-                    auto put = [&](int tx, int ty) { W.put((uint32_t)(ty * grid.gx + tx)); };
+                    // tiles x0..x1 of rows y0..y1, row-major: the order in
+                    // which every mode's tile function puts a whole rectangle
+                    auto rect = [&](int x0, int x1, int y0, int y1) {
+                        for (int ty = y0; ty <= y1; ++ty)
+                            for (int tx = x0; tx <= x1; ++tx) W.put((uint32_t)(ty * grid.gx + tx));
+                    };
                     if (kMode == GS_MODE_SNUGBOX) {
-                        for (int ty = S.R.y0; ty <= S.R.y1; ++ty)
-                            for (int tx = S.R.x0; tx <= S.R.x1; ++tx) W.put((uint32_t)(ty * grid.gx + tx));
+                        rect(S.R.x0, S.R.x1, S.R.y0, S.R.y1);
                     } else if (kMode == GS_MODE_TBC) {
-                        tbc_tiles(E, S, grid, put);
+                        // the count is the kept tiles of the SnugBox rectangle
+                        if (c == (S.R.x1 - S.R.x0 + 1) * (S.R.y1 - S.R.y0 + 1)) rect(S.R.x0, S.R.x1, S.R.y0, S.R.y1);
+                        else defer = true;
                     } else if (kMode == GS_MODE_PIXEL) {
-                        pixel_tiles(E, S, grid, put);
+                        // the count is the kept tiles of the pixel box's tile range
+                        PixBox P;
+                        if (pixel_box(S, grid, P) && c == (P.tx1 - P.tx0 + 1) * (P.ty1 - P.ty0 + 1))
+                            rect(P.tx0, P.tx1, P.ty0, P.ty1);
+                        else
+                            defer = true;
                     } else {
                         int k, j0, j1;
                         bool rows;
@@ -332,8 +345,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) emit_kernel(const EmitArgs A)
         rad = nrad;
     }
     if (kDefer && qn > 0) {
-        // one lane per queued Gaussian: the warp runs the sweeps of all four
-        // rounds side by side instead of once per round
+        // one lane per queued Gaussian: the warp runs the tile searches of all
+        // four rounds side by side instead of once per round
         __syncwarp();
         for (int b = 0; b < qn; b += 32) {
             if (b + lane < qn) {
@@ -347,7 +360,12 @@ __global__ void __launch_bounds__(kScanThreads, 4) emit_kernel(const EmitArgs A)
                 KeyWriter W{A.keys, A.vals, off, off + A.counts[i], __float_as_uint(a0.w), id, grid.gx, tile0};
                 const Ellipse E{a0.x, a0.y, a1.x, a1.y, a1.z, a1.w};
                 Snug S;
-                if (snugbox(E, grid, S)) accutile_sweep(E, S, grid, W);
+                if (snugbox(E, grid, S)) {
+                    auto put = [&](int tx, int ty) { W.put((uint32_t)(ty * grid.gx + tx)); };
+                    if (kMode == GS_MODE_TBC) tbc_tiles(E, S, grid, put);
+                    else if (kMode == GS_MODE_PIXEL) pixel_tiles(E, S, grid, put);
+                    else accutile_sweep(E, S, grid, W);
+                }
             }
         }
     }

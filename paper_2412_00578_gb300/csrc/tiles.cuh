@@ -234,8 +234,15 @@ __device__ __forceinline__ int tbc_tiles(const Ellipse& E, const Snug& S, const 
 // do not overlap or touch (possible only for needles thinner than a pixel)
 // is settled by testing its tiles' pixels one by one.  Row-major;
 // put(tx, ty) per kept tile.
-template <class Put>
-__device__ __forceinline__ int pixel_tiles(const Ellipse& E, const Snug& S, const Grid& g, Put&& put) {
+struct PixBox {
+    int x0, x1, y0, y1;      // pixels considered (inclusive)
+    int tx0, tx1, ty0, ty1;  // tiles holding them (inclusive)
+};
+
+// The pixels pixel_tiles considers (the SnugBox widened by one pixel on each
+// side, clipped to the image) and their tile range; false when no pixel is
+// left.  Every tile pixel_tiles keeps lies in that range.
+__device__ __forceinline__ bool pixel_box(const Snug& S, const Grid& g, PixBox& P) {
     auto lo_px = [](float e, int n) {
         const float f = floorf(e) - 1.0f;
         return f < 0.0f ? 0 : (f > (float)n ? n : (int)f);
@@ -244,11 +251,26 @@ __device__ __forceinline__ int pixel_tiles(const Ellipse& E, const Snug& S, cons
         const float f = floorf(e) + 1.0f;
         return f < 0.0f ? -1 : (f > (float)(n - 1) ? n - 1 : (int)f);
     };
-    const int x0 = lo_px(S.x0, g.W), x1 = hi_px(S.x1, g.W);
-    const int y0 = lo_px(S.y0, g.H), y1 = hi_px(S.y1, g.H);
-    if (x0 > x1 || y0 > y1) return 0;
+    P.x0 = lo_px(S.x0, g.W);
+    P.x1 = hi_px(S.x1, g.W);
+    P.y0 = lo_px(S.y0, g.H);
+    P.y1 = hi_px(S.y1, g.H);
+    if (P.x0 > P.x1 || P.y0 > P.y1) return false;
     const int T = (int)g.T;
-    const int tx0 = x0 / T, tx1 = x1 / T, ty0 = y0 / T, ty1 = y1 / T;
+    P.tx0 = P.x0 / T;
+    P.tx1 = P.x1 / T;
+    P.ty0 = P.y0 / T;
+    P.ty1 = P.y1 / T;
+    return true;
+}
+
+template <class Put>
+__device__ __forceinline__ int pixel_tiles(const Ellipse& E, const Snug& S, const Grid& g, Put&& put) {
+    PixBox P;
+    if (!pixel_box(S, g, P)) return 0;
+    const int x0 = P.x0, x1 = P.x1, y0 = P.y0, y1 = P.y1;
+    const int T = (int)g.T;
+    const int tx0 = P.tx0, tx1 = P.tx1, ty0 = P.ty0, ty1 = P.ty1;
     auto clampi = [](float f, int lo, int hi) { return !(f >= (float)lo) ? lo : (f > (float)hi ? hi : (int)f); };
     int cnt = 0;
     for (int ty = ty0; ty <= ty1; ++ty) {
