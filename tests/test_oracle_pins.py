@@ -277,6 +277,49 @@ def test_accutile_rows_equal_columns_and_nesting():
                 assert x * T > e[0] + r - 1 or y * T > e[1] + r - 1, (e, r, (x, y))
 
 
+@pytest.mark.parametrize("prec64", [False, True])
+def test_accutile_single_line_with_outer_boundaries_is_whole(prec64):
+    """Sec. 4.1.2, Algorithm 1: when the SnugBox tile rectangle is one tile
+    line thick on its shorter side and both boundaries of that line lie
+    outside the SnugBox span, the line holds the whole ellipse, so AccuTile
+    intersects no boundary and keeps the rectangle's whole span.  Checked on
+    the oracle's sweep (tiles and their order) and, in FP64, against the
+    brute-force set of tiles whose closed square meets the ellipse."""
+    rng = np.random.default_rng(17 + prec64)
+    T, gx, gy = 16, 20, 15
+    whole = other = cut = 0
+    for e in random_ellipses(rng, 3000, gx, gy, T):
+        ok, sb = oracle.snugbox(e, T, gx, gy, prec64)
+        if not ok:
+            continue
+        x0, x1, y0, y1 = sb[:4]
+        tx0, tx1, ty0, ty1 = (int(z) for z in sb[4:])
+        rows = (ty1 - ty0) <= (tx1 - tx0)
+        k0, k1 = (ty0, ty1) if rows else (tx0, tx1)
+        lo, hi = (y0, y1) if rows else (x0, x1)
+        got = [tuple(map(int, p)) for p in oracle.ellipse_tiles(e, ACCU, T, gx, gy, prec64)]
+        want = [(tx, ty) for ty in range(ty0, ty1 + 1) for tx in range(tx0, tx1 + 1)]
+        if k0 != k1:
+            other += 1
+            continue
+        if k0 * T >= lo or (k0 + 1) * T <= hi:
+            # a boundary inside the span (the rectangle clipped at an image
+            # edge across its line, or a box edge exactly on a tile edge):
+            # the line's extent may be shorter
+            cut += len(got) < len(want)
+            continue
+        assert got == want, (e, got, want)
+        if prec64:
+            mask = oracle.exact_tile_mask(e, T, gx, gy)
+            exact = {(x, y) for y, x in zip(*np.nonzero(mask))}
+            for (x, y) in exact ^ set(want):  # only tiles the ellipse just touches may differ
+                u, v, a, b, c, t = e
+                assert oracle.exact_tile_mask((u, v, a, b, c, t * (1 + 1e-7)), T, gx, gy)[y, x] != \
+                    oracle.exact_tile_mask((u, v, a, b, c, t * (1 - 1e-7)), T, gx, gy)[y, x], (e, (x, y))
+        whole += 1
+    assert whole > 300 and other > 300 and cut > 20, (whole, other, cut)
+
+
 def test_accutile_fp32_is_superset_of_fp32_pixels():
     """Every pixel whose FP32 blend test q <= t passes lies in a tile of the
     Gaussian's FP32 AccuTile set (the tile lists lose no contributing pixel);
@@ -536,7 +579,7 @@ def test_sigma3_golden_catches_planted_mistakes(mutant, tmp_path):
 TBC, PIX = 3, 4
 
 
-def random_ellipses(rng, count, T, gx, gy):
+def rotated_ellipses(rng, count, T, gx, gy):
     """Ellipses with random orientation, axis lengths from sub-pixel to a few
     tiles, centres over and around a gx x gy grid of T-pixel tiles."""
     out = []
@@ -563,7 +606,7 @@ def test_tbc_tile_test_against_numerical_minimum():
     rng = np.random.default_rng(91)
     T, gx, gy = 16, 6, 5
     checked = 0
-    for e in random_ellipses(rng, 150, T, gx, gy):
+    for e in rotated_ellipses(rng, 150, T, gx, gy):
         u, v, a, b, c, t = e
         ok, sb = oracle.snugbox(e, T, gx, gy, True)
         if not ok:
@@ -589,7 +632,7 @@ def test_tbc_and_accutile_are_the_same_exact_set():
     ellipse: equal on random ellipses and on the App. A.1 fixtures."""
     rng = np.random.default_rng(92)
     for T, gx, gy in ((16, 6, 5), (8, 9, 7)):
-        for e in random_ellipses(rng, 400, T, gx, gy):
+        for e in rotated_ellipses(rng, 400, T, gx, gy):
             tbc = tile_set(oracle.ellipse_tiles(e, TBC, T, gx, gy, True))
             acc = tile_set(oracle.ellipse_tiles(e, ACCU, T, gx, gy, True))
             assert tbc == acc, e
@@ -605,7 +648,7 @@ def test_pixel_tiles_against_whole_image_brute_force():
     W, H = gx * T, gy * T
     X, Y = np.meshgrid(np.arange(W), np.arange(H))
     surplus = total = 0
-    for e in random_ellipses(rng, 300, T, gx, gy):
+    for e in rotated_ellipses(rng, 300, T, gx, gy):
         u, v, a, b, c, t = e
         for prec64, dt in ((True, np.float64), (False, np.float32)):
             uu, vv, aa, bb, cc, tt = (dt(x) for x in e)
