@@ -671,6 +671,37 @@ def test_pixel_tiles_against_whole_image_brute_force():
     assert 0 < surplus < total
 
 
+@pytest.mark.parametrize("prec64", [False, True])
+def test_full_rectangles_are_listed_row_major(prec64):
+    """A tile set that fills its bounding rectangle is listed row by row,
+    left to right, in SnugBox, tile-based culling (the SnugBox rectangle
+    walked that way, App. A.4) and pixel-exact modes (tile row by tile row),
+    and for AccuTile when it is a single line; so a key writer that knows the
+    set is a whole rectangle may write it in that order.  AccuTile lists a
+    multi-line rectangle line by line along its sweep (columns when they are
+    the shorter side), so only its set is checked there."""
+    rng = np.random.default_rng(94 + prec64)
+    T, gx, gy = 8, 9, 7
+    full = {m: 0 for m in (SNUG, ACCU, TBC, PIX)}
+    for e in rotated_ellipses(rng, 400, T, gx, gy):
+        for m in full:
+            got = [tuple(map(int, p)) for p in oracle.ellipse_tiles(e, m, T, gx, gy, prec64)]
+            if not got:
+                continue
+            xs = [p[0] for p in got]
+            ys = [p[1] for p in got]
+            rect = [(x, y) for y in range(min(ys), max(ys) + 1) for x in range(min(xs), max(xs) + 1)]
+            if len(got) != len(rect):
+                continue
+            single = min(ys) == max(ys) or min(xs) == max(xs)
+            if m == ACCU and not single:
+                assert sorted(got) == sorted(rect)  # rows or columns, whichever is shorter
+                continue
+            assert got == rect, (m, e, got)
+            full[m] += 1
+    assert min(full.values()) > 50, full
+
+
 def test_new_modes_render_the_definition_image():
     """Tile-based culling and pixel-exact tiles lose no contributing pixel:
     their tiled images equal the tile-free image bit for bit, in FP32 and
