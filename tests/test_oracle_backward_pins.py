@@ -2,8 +2,6 @@
 differences of the oracle's own FP64 forward (a different code path: the
 forward never differentiates), the SH basis derivative against finite
 differences of the basis, and the pruning score against its closed form."""
-import math
-
 import numpy as np
 import torch
 import pytest

@@ -5,8 +5,6 @@ working memory in a fixed array built into the library instead of the
 frame's scratch buffer.  Checked here through the C ABI against gs_intersect
 on the same inputs, on two calls in a row (the second call runs on the array
 the first one left behind)."""
-import ctypes
-
 import numpy as np
 import pytest
 import torch
