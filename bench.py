@@ -465,11 +465,14 @@ def stage_work(st, n, n_counted, K, sh_bytes, hw, tiles, passes):
     """Algorithmic bytes per stage (the per-unit figures of the design notes
     times the units of this frame)."""
     return {
-        # geometry + opacity read and a 4 B count written for every Gaussian;
-        # SH read and the 48 B 2D state written for every counted one
-        "preprocess": n * (40 + 4) + n_counted * (sh_bytes + 48),
-        # counts read twice, 2D state read once per counted Gaussian, 12 B per key written
-        "intersect": n * 8 + n_counted * 48 + K * 12,
+        # geometry (40 B) and opacity (4 B) read and a 4 B count written for
+        # every Gaussian; SH read and the 48 B 2D state written for every
+        # counted one
+        "preprocess": n * (44 + 4) + n_counted * (sh_bytes + 48),
+        # counts read twice (scan, emit); the 32 B of 2D state the tile function
+        # needs (centre and depth; conic and threshold, or the 3-sigma radius)
+        # read once per counted Gaussian; 12 B per key written
+        "intersect": n * 8 + n_counted * 32 + K * 12,
         # lower bound: read and write every (key, value) pair once
         "sort": K * 24,
         # the onesweep design: one histogram read + 24 B per key and pass

@@ -6,7 +6,7 @@
 // tile reads the SH coefficients (192 of the 236 bytes of a Gaussian; they are
 // prefetched into L2 early, one prefetch per line and warp, so the late loads
 // do not wait on HBM) and writes the 48-byte 2D state.  Gaussians that are culled or off-screen cost
-// their 40 bytes of geometry and opacity plus a 4-byte count.
+// their 44 bytes of geometry and opacity plus a 4-byte count.
 #include "tiles.cuh"
 
 namespace gs {
