@@ -478,8 +478,9 @@ def stage_work(st, n, n_counted, K, sh_bytes, hw, tiles, passes):
         # the onesweep design: one histogram read + 24 B per key and pass
         "sort_design": K * 8 + K * 24 * passes,
         "tile_ranges": K * 8 + tiles * 8,
-        # blend memory traffic: index + 48 B gathered per key, 20 B per pixel written
-        "render": K * (4 + 48) + hw * 20,
+        # blend: each key's 4 B value and each counted Gaussian's 48 B of 2D
+        # state read once, 20 B per pixel written (image, final T, last index)
+        "render": K * 4 + n_counted * 48 + hw * 20,
     }
 
 
