@@ -338,6 +338,10 @@ def run_schedule(device, sch: Schedule | None = None, task: Task | None = None, 
            "iterations": sch.at(sch.iterations), "train_views": len(task.train), "test_views": len(task.test),
            "resolution": f"{task.train[0].width}x{task.train[0].height}", "gt_gaussians": task.gt.n,
            "init_gaussians": task.init.n}
+    # an untimed 20-iteration fit first, so neither timed fit carries the
+    # process's first-use set-up (library handles, allocator growth)
+    fit(task, device, sch, prune=False, iterations=20)
+    torch.cuda.synchronize()
     for name, prune in (("baseline", False), ("soft_hard", True)):
         t0 = time.perf_counter()
         model, events = fit(task, device, sch, prune=prune, log=log)
