@@ -36,3 +36,14 @@ def test_frame_sizes_without_gpu():
     for bad in [(1000, 320, 240, 12, 10), (1000, 0, 240, 16, 10), (1000, 320, 240, 16, 1 << 31)]:
         with pytest.raises(raster.GsError):
             raster.frame_sizes(*bad)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the compiled library the binding raises: there is no CPU path
+    to fall back on."""
+    import pytest
+
+    from paper_2412_00578_gb300 import raster
+
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        raster.load(tmp_path / "libgs.so")
