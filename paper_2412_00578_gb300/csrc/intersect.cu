@@ -7,11 +7,14 @@
 //                capacity overflow;
 //   emit         each block re-reads its 1024 counts, scans them in shared
 //                memory round by round (so per-Gaussian offsets are never
-//                stored in HBM), and every Gaussian with tiles recomputes its tile set with
-//                the same localization function the count used and writes
-//                its (tile << 32 | depth bits, index) pairs at its offset,
-//                in buffer 0, or (for a fused forward call) in the buffer
-//                the sort plan starts from (scan_top's offsets say which).
+//                stored in HBM), and every Gaussian with tiles writes its
+//                (tile << 32 | depth bits, index) pairs at its offset: a
+//                whole rectangle known in advance directly, any other tile
+//                set recomputed with the localization function the count
+//                used (those are queued per warp and searched after the
+//                rounds); in buffer 0, or (for a fused forward call) in the
+//                buffer the sort plan starts from (scan_top's offsets say
+//                which).
 #include "tiles.cuh"
 
 namespace gs {
