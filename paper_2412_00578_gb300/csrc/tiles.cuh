@@ -1,8 +1,11 @@
 // Gaussian-to-tile localization: the 3D-GS 3-sigma square (Eq. radius),
 // SnugBox (Sec. 4.1.1) and AccuTile (Sec. 4.1.2, Algorithm 1), as device
 // functions shared by the counting pass (preprocess) and the emitting pass
-// (duplicateWithKeys).  Both passes call the same function, so the count
-// always equals the number of keys emitted.
+// (duplicateWithKeys), plus tile-based culling (App. A.4) and pixel-exact
+// tiles.  Both passes call the same functions, so the count always equals the
+// number of keys emitted; where the emit writes a whole rectangle without
+// them, the count or a shared predicate (accutile_whole_line) has already
+// shown that the function's result is that rectangle.
 #pragma once
 
 #include "gs_common.cuh"
